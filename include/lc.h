@@ -1,0 +1,193 @@
+/*
+ * lc.h - C ABI of the GB300 lid-driven-cavity library.
+ *
+ * The library advances the two-dimensional incompressible Navier-Stokes
+ * equations in vorticity / stream-function form on the unit square with a
+ * moving lid, by the method of N. Cardoso and P. Bicudo, "Time dependent
+ * simulation of the Driven Lid Cavity at High Reynolds Number"
+ * (arXiv:0809.3098):
+ *   - vorticity transport, Sec. 2, Eq. (4); stream-function Poisson
+ *     equation, Eq. (3), discretised by the compact fourth-order scheme of
+ *     Eq. (14) (default) or the plain 5-point Laplacian;
+ *   - spatial operator L(omega), Sec. 3, Eq. (8), velocities from Eq. (22);
+ *   - SSPRK(5,4) time step, Sec. 3, Eqs. (9)-(13);
+ *   - psi = 0 on the walls, lid speed U, Thom's wall vorticity, Sec. 3.1,
+ *     Eq. (25);
+ *   - the Poisson equation is solved in every Runge-Kutta stage, warm-started
+ *     from the previous solve, by multigrid V-cycles whose smoother is the SOR
+ *     update of Eq. (15) in colour order (red-black for the 5-point operator,
+ *     four colours (i mod 2, j mod 2) for the compact one), until
+ *     ||f - L_h psi||_2 <= tol * ||f||_2 over interior nodes (checked after
+ *     every cycle, at least one cycle per solve);
+ *   - steady-state monitors RES_psi, RES_omega, Sec. 3.2, Eqs. (26)-(27).
+ *
+ * Grid and layout.  N is the number of intervals per side (h = 1/N); fields
+ * have (N+1) x (N+1) nodes.  Every host array exchanged through this ABI is
+ * FP64, row-major, index j*(N+1) + i, with i the x index (0 = left wall,
+ * N = right wall) and j the y index (0 = bottom wall, N = lid).  N must be
+ * 2^k or 3*2^k with 8 <= N <= 8192 (multigrid halves N down to 2 or 3).
+ *
+ * Time step.  One step is one SSPRK(5,4) step: five Runge-Kutta stages and
+ * five Poisson solves (psi is re-solved at the end of the step so that the
+ * (psi, omega) pair returned by the getters is consistent).  Wall vorticity
+ * is recomputed by Thom's formula after every solve and held fixed while L is
+ * evaluated; the compact right-hand side at wall-adjacent nodes uses the wall
+ * vorticity of the previous solve.
+ *
+ * Errors.  Functions returning int return LC_OK (0) or a negative LC_ERR_*
+ * code and never throw; lc_last_error() gives a message for the calling
+ * thread.  A NULL, destroyed or foreign context gives LC_ERR_ARG.
+ *
+ * Concurrency and ownership.  A context belongs to one host thread at a time.
+ * lc_step only enqueues work on the context's CUDA stream and returns; errors
+ * raised on the device by that work (LC_ERR_NOCONV, LC_ERR_NONFINITE) are
+ * reported by the next call that synchronises the stream (the getters,
+ * lc_residual, lc_monitor, lc_synchronize, lc_save).  Host buffers are owned
+ * by the caller and only read or written during the call.  Device memory is
+ * owned by the library unless the caller binds its own with
+ * lc_bind_workspace.
+ */
+#ifndef LC_H
+#define LC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LC_OK 0
+#define LC_ERR_ARG (-1)       /* invalid argument, NULL or destroyed context        */
+#define LC_ERR_CUDA (-2)      /* a CUDA runtime call failed                          */
+#define LC_ERR_NOCONV (-3)    /* a Poisson solve hit max_cycles above its tolerance  */
+#define LC_ERR_NONFINITE (-4) /* NaN or Inf appeared in a residual or the state      */
+#define LC_ERR_TIMEOUT (-5)   /* reserved: a bounded device-side wait gave up        */
+#define LC_ERR_SIZE (-6)      /* buffer too small or size out of range               */
+#define LC_ERR_IO (-7)        /* checkpoint file could not be read or written        */
+
+#define LC_OP_5PT 0     /* (delta_xx + delta_yy) psi = -omega                          */
+#define LC_OP_COMPACT 1 /* Eq. (14): compact fourth-order operator (default)           */
+
+#define LC_PREC_FP64 0  /* every kernel computes in FP64 (default)                     */
+#define LC_PREC_MIXED 1 /* FP32 smoothing and stencils inside FP64 residual/refinement */
+
+typedef struct lc_ctx lc_ctx;
+
+/* Creates a cavity at rest: omega = 0 in the interior, psi = 0, and the lid's
+ * Thom vorticity -2U/h on the top wall (U = 1).  Re > 0 is U L / nu with
+ * L = 1, so nu = 1/Re (Sec. 3.2).  dt > 0 is used as given; dt <= 0 selects
+ * dt = 0.25 min(h, Re h^2 / 4).  tol > 0 is the relative residual at which
+ * each Poisson solve stops.  Device memory is allocated (or taken from
+ * lc_bind_workspace) at the first call that needs it, on the device that is
+ * current at that time.  Returns NULL on error (see lc_last_error). */
+lc_ctx *lc_create(int N, double Re, double dt, double tol);
+
+/* Releases the context, its CUDA graph, stream and any memory it allocated
+ * (bound memory is left to the caller).  NULL is ignored. */
+void lc_destroy(lc_ctx *ctx);
+
+/* Enqueues nsteps >= 0 SSPRK(5,4) steps on the context's stream (one CUDA
+ * graph launch per step) and returns without waiting.  If the "monitor"
+ * option is 1 the monitors of lc_monitor are taken over the last of these
+ * steps. */
+int lc_step(lc_ctx *ctx, int nsteps);
+
+/* Copies psi / omega, (N+1)^2 FP64 values in the layout above, into a host
+ * buffer of n_elems >= (N+1)^2 elements (LC_ERR_SIZE otherwise).  Waits for
+ * the stream; returns the first pending device error. */
+int lc_get_psi(lc_ctx *ctx, double *host_out, size_t n_elems);
+int lc_get_omega(lc_ctx *ctx, double *host_out, size_t n_elems);
+
+/* Relative residual ||f - L_h psi|| / ||f|| at the end of the most recent
+ * Poisson solve (waits for the stream).  NaN for an invalid context. */
+double lc_residual(lc_ctx *ctx);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *lc_last_error(void);
+
+/* Sets an option; value is converted to the option's type.  Keys:
+ *   "op"          LC_OP_5PT or LC_OP_COMPACT (default)       [before first use]
+ *   "precision"   LC_PREC_FP64 (default) or LC_PREC_MIXED   [before first use]
+ *   "nu1","nu2"   pre/post smoothing sweeps per level (2, 2), 1..16
+ *   "nuc"         sweeps on the coarsest grid (16), 1..256
+ *   "beta"        relaxation of the SOR update, Eq. (15) (1.0), 0 < beta < 2
+ *   "max_cycles"  V-cycle cap per solve (100); hitting it raises LC_ERR_NOCONV
+ *   "U"           lid speed (1.0); re-applies Thom to the current state
+ *   "profile"     0 uniform lid (default), 1 regularised lid 16x^2(1-x)^2 U
+ *   "advect"      1 (default), 0 drops the transport terms of Eq. (8)
+ *   "monitor"     1 computes lc_monitor's values over the last step of each
+ *                 lc_step call (default 0)
+ * Returns LC_ERR_ARG for an unknown key or a value out of range. */
+int lc_set_option(lc_ctx *ctx, const char *key, double value);
+
+/* Makes the context enqueue all later work on cuda_stream (a cudaStream_t,
+ * e.g. torch.cuda.current_stream().cuda_stream); NULL is the legacy default
+ * stream.  Until this is called the context uses a non-blocking stream of
+ * its own.  Work already enqueued is ordered before work on the new stream.
+ * The caller keeps the stream alive while the context uses it. */
+int lc_set_stream(lc_ctx *ctx, void *cuda_stream);
+
+/* Bytes of device memory a context of size N and precision needs (0 if the
+ * arguments are invalid). */
+size_t lc_workspace_bytes(int N, int precision);
+
+/* Gives the context caller-owned device memory (256-byte aligned, at least
+ * lc_workspace_bytes(N, precision) bytes) instead of allocating its own.
+ * Must come before the first use of the context; the caller keeps the memory
+ * alive until lc_destroy.  LC_ERR_SIZE if too small or misaligned. */
+int lc_bind_workspace(lc_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* out[0] = max |omega^{n+1} - omega^n| / dt, out[1] = RES_psi,
+ * out[2] = RES_omega (Eqs. (26)-(27), with 1/N read as 1/(N+1), the points
+ * per side), out[3] = V-cycles of the last Poisson solve; taken over the
+ * last step of the most recent lc_step call with the "monitor" option on
+ * (zeros otherwise).  Waits for the stream. */
+int lc_monitor(lc_ctx *ctx, double out[4]);
+
+/* Installs a state from host arrays ((N+1)^2 FP64 each).  psi is taken as
+ * given (its walls are forced to zero); omega's interior is taken and its
+ * walls are recomputed from psi by Thom's formula, Eq. (25).  The next step
+ * uses psi as the solution for omega (no solve at the first stage). */
+int lc_set_state(lc_ctx *ctx, const double *psi, const double *omega);
+
+/* Checkpoint: writes / reads a binary file holding a header (magic "LCCK",
+ * version, N, Re, dt, tol, U, steps taken, precision, operator) and the FP64
+ * psi and omega in the host layout.  lc_load requires the same N and sets the
+ * state as lc_set_state does.  LC_ERR_IO on file errors. */
+int lc_save(lc_ctx *ctx, const char *path);
+int lc_load(lc_ctx *ctx, const char *path);
+
+/* Copies the V-cycle count of each Poisson solve enqueued so far (oldest
+ * first, at most the last 65536) into out[0..max); *n_out receives the
+ * number copied.  Waits for the stream. */
+int lc_cycle_log(lc_ctx *ctx, int *out, size_t max, size_t *n_out);
+
+/* Waits for the context's stream; returns the first pending device error. */
+int lc_synchronize(lc_ctx *ctx);
+
+/* Reads back the resolved parameters: out[0] = N, out[1] = Re, out[2] = dt,
+ * out[3] = tol, out[4] = h, out[5] = multigrid levels, out[6] = steps taken. */
+int lc_get_params(lc_ctx *ctx, double out[7]);
+
+/* Kernel launches the context enqueues: out[0] per step outside the Poisson
+ * loops, out[1] per V-cycle of a Poisson loop (its residual norm and finisher
+ * included).  A step therefore launches out[0] + out[1] * (V-cycles of its
+ * five solves); lc_cycle_log gives the cycles. */
+int lc_launch_stats(lc_ctx *ctx, double out[2]);
+
+/* Roofline diagnostics: times `reps` >= 1 back-to-back launches of one kernel
+ * of the step, with the arguments it has inside the step, between CUDA events
+ * on the context stream.  kernel 0 = fine-level smoother colour phase (the
+ * colours taken in turn), 1 = fused L(omega) + stage combination (stage 2),
+ * 2 = fine-level residual + full-weighting restriction.  out[0] = mean ms per
+ * launch, out[1] = algorithmic bytes per launch (each array element the
+ * kernel must read or write, counted once), out[2] = FP64 and out[3] = FP32
+ * floating-point operations per launch (an FMA counts two).  The launches
+ * change the state: use only on a context whose state no longer matters. */
+int lc_bench_kernel(lc_ctx *ctx, int kernel, int reps, double out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LC_H */

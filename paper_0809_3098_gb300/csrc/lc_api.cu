@@ -1,0 +1,715 @@
+// C ABI of the cavity library (declared in include/lc.h): context, device
+// workspace, the per-step CUDA graph and the host entry points.
+//
+// One time step is captured once into a CUDA graph and replayed:
+//   for stage k = 1..5 (Eqs. (9)-(13)):
+//     fused L(omega) + stage combination            (k_rhs_stage)
+//     Poisson right-hand side from the new omega    (k_assemble_rhs, Eq. (14)/(17))
+//     while-node: V-cycle; residual norm; finisher  (Eq. (15) smoother, stopping rule)
+//     Thom wall vorticity                           (k_thom, Eq. (25))
+// The V-cycle loop is a CUDA graph conditional while-node whose condition is
+// set on the device by the finisher, so a solve never returns to the host.
+#include "lc_internal.h"
+
+#include "../../include/lc.h"
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+using namespace lcx;
+
+namespace {
+
+thread_local std::string g_err;
+std::mutex g_live_mu;
+std::set<const void *> g_live;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return LC_ERR_CUDA;
+}
+
+#define LC_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// SSPRK(5,4) Shu-Osher coefficients, Eqs. (9)-(13).  The omega^(1) weight of
+// Eq. (10) is printed 0.555626506348765; the stage's weights sum to one, so it
+// is 1 - 0.444370493651235 = 0.555629506348765.  Eq. (9)'s 11-digit
+// 0.39175222657 is carried to 0.391752226571890.
+constexpr double A20 = 0.444370493651235, A21 = 0.555629506348765;
+constexpr double A30 = 0.620101851488403, A32 = 0.379898148511597;
+constexpr double A40 = 0.178079954393132, A43 = 0.821920045606868;
+constexpr double A52 = 0.517231671970585, A53 = 0.096059710526147, A54 = 0.386708617503269;
+constexpr double B10 = 0.391752226571890, B21 = 0.368410593050371, B32 = 0.251891774271694;
+constexpr double B43 = 0.544974750228521, B53 = 0.063692468666290, B54 = 0.226007483236906;
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+int pitch_of(int N) { return ((N + 1 + 31) / 32) * 32; }
+
+int level_count(int N) {
+    int n = 1;
+    while (N % 2 == 0 && N >= 4) {
+        N /= 2;
+        ++n;
+    }
+    return (N == 2 || N == 3) ? n : -1;
+}
+
+bool valid_N(int N) { return N >= 8 && N <= 8192 && level_count(N) >= 2; }
+
+// Offsets of every device array inside one workspace block.
+struct Layout {
+    int nlev = 0;
+    int Nl[kMaxLevels], Pl[kMaxLevels];
+    size_t psi[kMaxLevels], g[kMaxLevels];
+    size_t W0, Wa, Wb, ACC, snap_psi, snap_w;
+    size_t rpart, gpart, mpart, ds;
+    int nrpart, ngpart, nmpart;
+    size_t total = 0;
+};
+
+bool make_layout(int N, int precision, Layout &L) {
+    if (!valid_N(N) || (precision != LC_PREC_FP64 && precision != LC_PREC_MIXED)) return false;
+    L.nlev = level_count(N);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    for (int l = 0; l < L.nlev; ++l) {
+        L.Nl[l] = N >> l;
+        L.Pl[l] = pitch_of(L.Nl[l]);
+        size_t n = (size_t)(L.Nl[l] + 1) * L.Pl[l];
+        L.psi[l] = take(n * sizeof(double));
+        L.g[l] = take(n * sizeof(double));
+    }
+    size_t n0 = (size_t)(N + 1) * L.Pl[0] * sizeof(double);
+    L.W0 = take(n0);
+    L.Wa = take(n0);
+    L.Wb = take(n0);
+    L.ACC = take(n0);
+    L.snap_psi = take(n0);
+    L.snap_w = take(n0);
+    L.nrpart = residual_norm_blocks(N);
+    L.ngpart = assemble_blocks(N);
+    L.nmpart = monitor_blocks(N);
+    L.rpart = take(L.nrpart * sizeof(double));
+    L.gpart = take(L.ngpart * sizeof(double));
+    L.mpart = take(3 * L.nmpart * sizeof(double) + 16);
+    L.ds = take(sizeof(DevState));
+    L.total = off;
+    return true;
+}
+
+}  // namespace
+
+struct lc_ctx {
+    int N;
+    double Re, dt, tol;
+    int op = LC_OP_COMPACT, precision = LC_PREC_FP64;
+    int nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
+    double beta = 1.0, U = 1.0;
+
+    Layout lay;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false, initialized = false;
+    int device = -1;
+
+    cudaStream_t own_stream = nullptr, user_stream = nullptr;
+    bool use_user_stream = false;
+    cudaStream_t cap2 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool graph_dirty = true;
+
+    long long steps = 0;
+    bool mon_valid = false;
+    int kernels_per_cycle = 0, kernels_per_step = 0;
+
+    cudaStream_t stream() const { return use_user_stream ? user_stream : own_stream; }
+    template <typename T>
+    T *at(size_t off) const {
+        return reinterpret_cast<T *>(ws + off);
+    }
+    double *psi(int l) const { return at<double>(lay.psi[l]); }
+    double *g(int l) const { return at<double>(lay.g[l]); }
+    DevState *ds() const { return at<DevState>(lay.ds); }
+};
+
+namespace {
+
+bool live(const lc_ctx *c) {
+    std::lock_guard<std::mutex> lk(g_live_mu);
+    return c && g_live.count(c);
+}
+
+#define LC_CHECK_CTX(c)                                           \
+    do {                                                          \
+        if (!live(c)) return fail(LC_ERR_ARG, "invalid context"); \
+    } while (0)
+
+void release_graph(lc_ctx *c) {
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+    c->graph_dirty = true;
+}
+
+// Enqueues one V-cycle (FP64) on stream s.
+int enqueue_vcycle(lc_ctx *c, cudaStream_t s) {
+    const Layout &L = c->lay;
+    int nc = c->op == LC_OP_COMPACT ? 4 : 2;
+    c->kernels_per_cycle = (L.nlev - 1) * ((c->nu1 + c->nu2) * nc + 2) + 1 + 2;  // + coarsest, norm, finisher
+    for (int l = 0; l + 1 < L.nlev; ++l) {
+        for (int sw = 0; sw < c->nu1; ++sw)
+            for (int col = 0; col < nc; ++col)
+                LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], col, c->beta));
+        LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], c->g(l + 1),
+                                                 c->psi(l + 1), L.Pl[l + 1]));
+    }
+    int lc = L.nlev - 1;
+    LC_CUDA(launch_coarsest<double>(s, c->op, c->psi(lc), c->g(lc), L.Nl[lc], L.Pl[lc], c->nuc, c->beta));
+    for (int l = L.nlev - 2; l >= 0; --l) {
+        LC_CUDA(launch_prolong_correct<double>(s, c->psi(l), L.Nl[l], L.Pl[l], c->psi(l + 1), L.Pl[l + 1]));
+        for (int sw = 0; sw < c->nu2; ++sw)
+            for (int col = 0; col < nc; ++col)
+                LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], col, c->beta));
+    }
+    return LC_OK;
+}
+
+// Captures: right-hand side of omega_buf, the V-cycle while-loop, Thom.
+int capture_solve(lc_ctx *c, cudaStream_t s, double *omega_buf) {
+    const Layout &L = c->lay;
+    int N = c->N, P = L.Pl[0];
+    LC_CUDA(launch_assemble_rhs(s, c->op, omega_buf, c->g(0), N, P, c->at<double>(L.gpart)));
+
+    cudaStreamCaptureStatus st;
+    cudaGraph_t g;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t ndeps = 0;
+    LC_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h;
+    LC_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    LC_CUDA(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    LC_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+
+    LC_CUDA(cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_vcycle(c, c->cap2);
+    if (rc == LC_OK) {
+        cudaError_t e = launch_residual_norm<double>(c->cap2, c->op, c->psi(0), c->g(0), N, P, c->at<double>(L.rpart));
+        if (e == cudaSuccess)
+            e = launch_finish_norm(c->cap2, c->at<double>(L.rpart), L.nrpart, c->at<double>(L.gpart), L.ngpart,
+                                   c->ds(), h, c->tol, c->max_cycles);
+        if (e != cudaSuccess) rc = cuda_fail(e, "body launch");
+    }
+    cudaGraph_t tmp = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(c->cap2, &tmp);
+    if (rc != LC_OK) return rc;
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture(body)");
+
+    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), N, P, c->U,
+                        c->profile));
+    return LC_OK;
+}
+
+int build_graph(lc_ctx *c) {
+    release_graph(c);
+    const Layout &L = c->lay;
+    int N = c->N, P = L.Pl[0];
+    double *W0 = c->at<double>(L.W0), *Wa = c->at<double>(L.Wa), *Wb = c->at<double>(L.Wb);
+    double *ACC = c->at<double>(L.ACC), *psi = c->psi(0);
+    double dt = c->dt;
+    StageCoef k1{1.0, 0.0, B10 * dt, 0.0, 0.0, 0};
+    StageCoef k2{A20, A21, B21 * dt, 0.0, 0.0, 0};
+    StageCoef k3{A30, A32, B32 * dt, A52, 0.0, 1};
+    StageCoef k4{A40, A43, B43 * dt, A53, B53 * dt, 2};
+    StageCoef k5{0.0, A54, B54 * dt, 0.0, 0.0, 3};
+    struct {
+        const double *in;
+        double *out;
+        StageCoef k;
+    } stages[5] = {{W0, Wa, k1}, {Wa, Wb, k2}, {Wb, Wa, k3}, {Wa, Wb, k4}, {Wb, W0, k5}};
+
+    cudaStream_t s;
+    LC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    int rc = LC_OK;
+    for (int k = 0; k < 5 && rc == LC_OK; ++k) {
+        cudaError_t le = launch_rhs_stage(s, psi, stages[k].in, W0, ACC, stages[k].out, N, P, c->Re, c->advect,
+                                          stages[k].k);
+        if (le != cudaSuccess) rc = cuda_fail(le, "launch_rhs_stage");
+        if (rc == LC_OK) rc = capture_solve(c, s, stages[k].out);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    cudaStreamDestroy(s);
+    if (rc != LC_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    c->graph = g;
+    c->kernels_per_step = 5 * 3;  // per stage: L + combination, Poisson right-hand side, Thom
+    LC_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
+    c->graph_dirty = false;
+    return LC_OK;
+}
+
+int ensure_init(lc_ctx *c) {
+    if (c->initialized) return LC_OK;
+    LC_CUDA(cudaGetDevice(&c->device));
+    if (!c->ws) {
+        void *p = nullptr;
+        LC_CUDA(cudaMalloc(&p, c->lay.total));
+        c->ws = static_cast<char *>(p);
+        c->ws_bytes = c->lay.total;
+        c->ws_owned = true;
+    }
+    if (!c->own_stream) LC_CUDA(cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking));
+    if (!c->cap2) LC_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
+    cudaStream_t s = c->stream();
+    LC_CUDA(cudaMemsetAsync(c->ws, 0, c->lay.total, s));
+    const Layout &L = c->lay;
+    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), c->N, L.Pl[0],
+                        c->U, c->profile));
+    c->initialized = true;
+    return LC_OK;
+}
+
+// Reads the device state after a stream sync and turns status bits into an error.
+int sync_status(lc_ctx *c) {
+    if (!c->initialized) return LC_OK;
+    LC_CUDA(cudaStreamSynchronize(c->stream()));
+    int status = 0;
+    LC_CUDA(cudaMemcpy(&status, &c->ds()->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status) {
+        int zero = 0;
+        LC_CUDA(cudaMemcpy(&c->ds()->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
+        if (status & kStatusNonFinite) return fail(LC_ERR_NONFINITE, "non-finite value in the Poisson residual or state");
+        if (status & kStatusNoConv) return fail(LC_ERR_NOCONV, "a Poisson solve reached max_cycles above tol");
+    }
+    return LC_OK;
+}
+
+int copy_field_out(lc_ctx *c, size_t off, double *host, size_t n) {
+    size_t need = (size_t)(c->N + 1) * (c->N + 1);
+    if (!host) return fail(LC_ERR_ARG, "NULL host buffer");
+    if (n < need) return fail(LC_ERR_SIZE, "host buffer smaller than (N+1)^2");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    LC_CUDA(cudaMemcpy2DAsync(host, (c->N + 1) * sizeof(double), c->at<double>(off), c->lay.Pl[0] * sizeof(double),
+                              (c->N + 1) * sizeof(double), c->N + 1, cudaMemcpyDeviceToHost, c->stream()));
+    return sync_status(c);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+lc_ctx *lc_create(int N, double Re, double dt, double tol) {
+    if (!valid_N(N)) {
+        fail(LC_ERR_ARG, "N must be 2^k or 3*2^k with 8 <= N <= 8192");
+        return nullptr;
+    }
+    if (!(Re > 0.0) || !std::isfinite(Re) || !(tol > 0.0) || !std::isfinite(dt)) {
+        fail(LC_ERR_ARG, "Re and tol must be positive and finite");
+        return nullptr;
+    }
+    double h = 1.0 / N;
+    if (dt <= 0.0) dt = 0.25 * std::fmin(h, Re * h * h / 4.0);
+    lc_ctx *c = new lc_ctx();
+    c->N = N;
+    c->Re = Re;
+    c->dt = dt;
+    c->tol = tol;
+    make_layout(N, c->precision, c->lay);
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live.insert(c);
+    }
+    g_err.clear();
+    return c;
+}
+
+void lc_destroy(lc_ctx *c) {
+    if (!live(c)) return;
+    {
+        std::lock_guard<std::mutex> lk(g_live_mu);
+        g_live.erase(c);
+    }
+    if (c->initialized) cudaStreamSynchronize(c->stream());
+    release_graph(c);
+    if (c->ws_owned && c->ws) cudaFree(c->ws);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    if (c->cap2) cudaStreamDestroy(c->cap2);
+    delete c;
+}
+
+const char *lc_last_error(void) { return g_err.c_str(); }
+
+size_t lc_workspace_bytes(int N, int precision) {
+    Layout L;
+    return make_layout(N, precision, L) ? L.total : 0;
+}
+
+int lc_bind_workspace(lc_ctx *c, void *dev_ptr, size_t bytes) {
+    LC_CHECK_CTX(c);
+    if (c->initialized) return fail(LC_ERR_ARG, "workspace must be bound before first use");
+    if (!dev_ptr || (reinterpret_cast<uintptr_t>(dev_ptr) & 255)) return fail(LC_ERR_SIZE, "workspace must be 256-byte aligned");
+    if (bytes < c->lay.total) return fail(LC_ERR_SIZE, "workspace smaller than lc_workspace_bytes");
+    c->ws = static_cast<char *>(dev_ptr);
+    c->ws_bytes = bytes;
+    c->ws_owned = false;
+    return LC_OK;
+}
+
+int lc_set_stream(lc_ctx *c, void *stream) {
+    LC_CHECK_CTX(c);
+    if (c->initialized) {
+        // order the old stream's work before anything on the new one
+        cudaEvent_t ev;
+        LC_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        LC_CUDA(cudaEventRecord(ev, c->stream()));
+        c->user_stream = static_cast<cudaStream_t>(stream);
+        c->use_user_stream = true;
+        LC_CUDA(cudaStreamWaitEvent(c->stream(), ev, 0));
+        LC_CUDA(cudaEventDestroy(ev));
+    } else {
+        c->user_stream = static_cast<cudaStream_t>(stream);
+        c->use_user_stream = true;
+    }
+    return LC_OK;
+}
+
+int lc_set_option(lc_ctx *c, const char *key, double v) {
+    LC_CHECK_CTX(c);
+    if (!key) return fail(LC_ERR_ARG, "NULL option key");
+    std::string k(key);
+    int iv = (int)v;
+    bool integral = v == (double)iv;
+    if (k == "op") {
+        if (c->initialized) return fail(LC_ERR_ARG, "op must be set before first use");
+        if (!integral || (iv != LC_OP_5PT && iv != LC_OP_COMPACT)) return fail(LC_ERR_ARG, "op must be 0 or 1");
+        c->op = iv;
+    } else if (k == "precision") {
+        if (c->initialized) return fail(LC_ERR_ARG, "precision must be set before first use");
+        if (!integral || (iv != LC_PREC_FP64 && iv != LC_PREC_MIXED)) return fail(LC_ERR_ARG, "precision must be 0 or 1");
+        if (iv == LC_PREC_MIXED) return fail(LC_ERR_ARG, "mixed precision is not available in this build");
+        c->precision = iv;
+        make_layout(c->N, c->precision, c->lay);
+    } else if (k == "nu1" || k == "nu2") {
+        if (!integral || iv < 1 || iv > 16) return fail(LC_ERR_ARG, "nu1/nu2 must be 1..16");
+        (k == "nu1" ? c->nu1 : c->nu2) = iv;
+    } else if (k == "nuc") {
+        if (!integral || iv < 1 || iv > 256) return fail(LC_ERR_ARG, "nuc must be 1..256");
+        c->nuc = iv;
+    } else if (k == "beta") {
+        if (!(v > 0.0 && v < 2.0)) return fail(LC_ERR_ARG, "beta must be in (0, 2)");
+        c->beta = v;
+    } else if (k == "max_cycles") {
+        if (!integral || iv < 1) return fail(LC_ERR_ARG, "max_cycles must be >= 1");
+        c->max_cycles = iv;
+    } else if (k == "U" || k == "profile") {
+        if (k == "U") {
+            if (!std::isfinite(v)) return fail(LC_ERR_ARG, "U must be finite");
+            c->U = v;
+        } else {
+            if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "profile must be 0 or 1");
+            c->profile = iv;
+        }
+        if (c->initialized) {
+            const Layout &L = c->lay;
+            LC_CUDA(launch_thom(c->stream(), c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa),
+                                c->at<double>(L.Wb), c->N, L.Pl[0], c->U, c->profile));
+        }
+    } else if (k == "advect") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "advect must be 0 or 1");
+        c->advect = iv;
+    } else if (k == "monitor") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "monitor must be 0 or 1");
+        c->monitor = iv;
+        return LC_OK;
+    } else {
+        return fail(LC_ERR_ARG, "unknown option " + k);
+    }
+    c->graph_dirty = true;
+    return LC_OK;
+}
+
+int lc_step(lc_ctx *c, int nsteps) {
+    LC_CHECK_CTX(c);
+    if (nsteps < 0) return fail(LC_ERR_ARG, "nsteps must be >= 0");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    if (c->graph_dirty) {
+        rc = build_graph(c);
+        if (rc) return rc;
+    }
+    cudaStream_t s = c->stream();
+    const Layout &L = c->lay;
+    size_t rowb = (size_t)L.Pl[0] * sizeof(double), fb = rowb * (c->N + 1);
+    for (int n = 0; n < nsteps; ++n) {
+        bool last = n == nsteps - 1;
+        if (last && c->monitor) {
+            LC_CUDA(cudaMemcpyAsync(c->at<double>(L.snap_psi), c->psi(0), fb, cudaMemcpyDeviceToDevice, s));
+            LC_CUDA(cudaMemcpyAsync(c->at<double>(L.snap_w), c->at<double>(L.W0), fb, cudaMemcpyDeviceToDevice, s));
+        }
+        LC_CUDA(cudaGraphLaunch(c->exec, s));
+        if (last && c->monitor) {
+            LC_CUDA(launch_monitor(s, c->at<double>(L.snap_psi), c->psi(0), c->at<double>(L.snap_w),
+                                   c->at<double>(L.W0), c->N, L.Pl[0], c->at<double>(L.mpart), c->ds(), c->dt));
+            c->mon_valid = true;
+        }
+        c->steps++;
+    }
+    return LC_OK;
+}
+
+int lc_get_psi(lc_ctx *c, double *host, size_t n) {
+    LC_CHECK_CTX(c);
+    return copy_field_out(c, c->lay.psi[0], host, n);
+}
+
+int lc_get_omega(lc_ctx *c, double *host, size_t n) {
+    LC_CHECK_CTX(c);
+    return copy_field_out(c, c->lay.W0, host, n);
+}
+
+double lc_residual(lc_ctx *c) {
+    if (!live(c)) {
+        fail(LC_ERR_ARG, "invalid context");
+        return NAN;
+    }
+    // device errors stay pending for the next int-returning call
+    if (ensure_init(c) != LC_OK || cudaStreamSynchronize(c->stream()) != cudaSuccess) return NAN;
+    double rel = 0.0;
+    if (cudaMemcpy(&rel, &c->ds()->last_rel, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) return NAN;
+    return rel;
+}
+
+int lc_synchronize(lc_ctx *c) {
+    LC_CHECK_CTX(c);
+    return sync_status(c);
+}
+
+int lc_monitor(lc_ctx *c, double out[4]) {
+    LC_CHECK_CTX(c);
+    if (!out) return fail(LC_ERR_ARG, "NULL output");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    rc = sync_status(c);
+    DevState head;
+    LC_CUDA(cudaMemcpy(&head, c->ds(), offsetof(DevState, log), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 3; ++k) out[k] = c->mon_valid ? head.mon[k] : 0.0;
+    out[3] = head.last_cycles;
+    return rc;
+}
+
+int lc_set_state(lc_ctx *c, const double *psi, const double *omega) {
+    LC_CHECK_CTX(c);
+    if (!psi || !omega) return fail(LC_ERR_ARG, "NULL state array");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    cudaStream_t s = c->stream();
+    const Layout &L = c->lay;
+    size_t hp = (c->N + 1) * sizeof(double), dp = L.Pl[0] * sizeof(double);
+    LC_CUDA(cudaMemcpy2DAsync(c->psi(0), dp, psi, hp, hp, c->N + 1, cudaMemcpyHostToDevice, s));
+    LC_CUDA(launch_zero_walls(s, c->psi(0), c->N, L.Pl[0]));
+    LC_CUDA(cudaMemcpy2DAsync(c->at<double>(L.W0), dp, omega, hp, hp, c->N + 1, cudaMemcpyHostToDevice, s));
+    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), c->N, L.Pl[0],
+                        c->U, c->profile));
+    LC_CUDA(cudaStreamSynchronize(s));  // the host arrays may be released on return
+    return LC_OK;
+}
+
+int lc_cycle_log(lc_ctx *c, int *out, size_t max, size_t *n_out) {
+    LC_CHECK_CTX(c);
+    if (!out || !n_out) return fail(LC_ERR_ARG, "NULL output");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    rc = sync_status(c);
+    DevState head;
+    LC_CUDA(cudaMemcpy(&head, c->ds(), offsetof(DevState, log), cudaMemcpyDeviceToHost));
+    std::vector<int> ring(kLogN);
+    LC_CUDA(cudaMemcpy(ring.data(), c->ds()->log, sizeof(int) * kLogN, cudaMemcpyDeviceToHost));
+    unsigned long long total = head.nsolves, avail = total < (unsigned long long)kLogN ? total : kLogN;
+    size_t n = avail < max ? (size_t)avail : max;
+    for (size_t k = 0; k < n; ++k) out[k] = ring[(total - avail + k) % kLogN];
+    *n_out = n;
+    return rc;
+}
+
+int lc_get_params(lc_ctx *c, double out[7]) {
+    LC_CHECK_CTX(c);
+    if (!out) return fail(LC_ERR_ARG, "NULL output");
+    out[0] = c->N;
+    out[1] = c->Re;
+    out[2] = c->dt;
+    out[3] = c->tol;
+    out[4] = 1.0 / c->N;
+    out[5] = c->lay.nlev;
+    out[6] = (double)c->steps;
+    return LC_OK;
+}
+
+int lc_launch_stats(lc_ctx *c, double out[2]) {
+    LC_CHECK_CTX(c);
+    if (!out) return fail(LC_ERR_ARG, "NULL output");
+    if (c->graph_dirty) {
+        int rc = ensure_init(c);
+        if (rc == LC_OK) rc = build_graph(c);
+        if (rc) return rc;
+    }
+    out[0] = c->kernels_per_step + (c->monitor ? 1 : 0);
+    out[1] = c->kernels_per_cycle;
+    return LC_OK;
+}
+
+int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
+    LC_CHECK_CTX(c);
+    if (!out || reps < 1 || kernel < 0 || kernel > 2) return fail(LC_ERR_ARG, "bad kernel id, reps or output");
+    int rc = ensure_init(c);
+    if (rc) return rc;
+    cudaStream_t s = c->stream();
+    const Layout &L = c->lay;
+    int N = c->N, P = L.Pl[0];
+    double n_int = (double)(N - 1) * (N - 1);
+    cudaEvent_t e0, e1;
+    LC_CUDA(cudaEventCreate(&e0));
+    LC_CUDA(cudaEventCreate(&e1));
+    int ncol = c->op == LC_OP_COMPACT ? 4 : 2;
+    auto launch = [&](int r) -> cudaError_t {
+        switch (kernel) {
+            case 0:
+                return launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), N, P, r % ncol, c->beta);
+            case 1: {
+                StageCoef k2{A20, A21, B21 * c->dt, 0.0, 0.0, 0};
+                return launch_rhs_stage(s, c->psi(0), c->at<double>(L.Wa), c->at<double>(L.W0), c->at<double>(L.ACC),
+                                        c->at<double>(L.Wb), N, P, c->Re, c->advect, k2);
+            }
+            default:
+                return launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), N, P, c->g(1), c->psi(1),
+                                                        L.Pl[1]);
+        }
+    };
+    LC_CUDA(launch(0));  // warm the instruction cache
+    LC_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < reps; ++r) LC_CUDA(launch(r));
+    LC_CUDA(cudaEventRecord(e1, s));
+    LC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    LC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    out[0] = ms / reps;
+    switch (kernel) {
+        case 0: {  // read psi once, read g and write psi at the colour's nodes
+            double nc = n_int / ncol;
+            out[1] = 8.0 * n_int + 16.0 * nc;
+            // compact: 6 adds + 2 FMAs; 5-point: 3 adds + 1 FMA; relaxation adds a subtract and an FMA
+            double per = (c->op == LC_OP_COMPACT ? 10.0 : 5.0) + (c->beta != 1.0 ? 3.0 : 0.0);
+            out[2] = per * nc;
+            out[3] = 0.0;
+            break;
+        }
+        case 1:  // stage 2: read omega^(1), psi, omega^n; write omega^(2)
+            out[1] = 32.0 * n_int;
+            out[2] = (c->advect ? 27.0 : 13.0) * n_int;
+            out[3] = 0.0;
+            break;
+        default:  // read psi, g; write the coarse g and zero the coarse psi
+            out[1] = 16.0 * n_int + 16.0 * (N / 2 - 1) * (N / 2 - 1);
+            out[2] = (c->op == LC_OP_COMPACT ? 11.0 : 6.0) * n_int + 8.0 * (N / 2 - 1) * (N / 2 - 1);
+            out[3] = 0.0;
+    }
+    return LC_OK;
+}
+
+struct CkptHeader {
+    char magic[4];
+    int version, N, precision, op, pad;
+    double Re, dt, tol, U;
+    long long steps;
+};
+
+int lc_save(lc_ctx *c, const char *path) {
+    LC_CHECK_CTX(c);
+    if (!path) return fail(LC_ERR_ARG, "NULL path");
+    size_t n = (size_t)(c->N + 1) * (c->N + 1);
+    std::vector<double> psi(n), w(n);
+    int rc = lc_get_psi(c, psi.data(), n);
+    if (rc) return rc;
+    rc = lc_get_omega(c, w.data(), n);
+    if (rc) return rc;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, "LCCK", 4);
+    h.version = 1;
+    h.N = c->N;
+    h.precision = c->precision;
+    h.op = c->op;
+    h.Re = c->Re;
+    h.dt = c->dt;
+    h.tol = c->tol;
+    h.U = c->U;
+    h.steps = c->steps;
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(LC_ERR_IO, std::string("cannot open ") + path);
+    bool ok = fwrite(&h, sizeof(h), 1, f) == 1 && fwrite(psi.data(), sizeof(double), n, f) == n &&
+              fwrite(w.data(), sizeof(double), n, f) == n;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? LC_OK : fail(LC_ERR_IO, "short write");
+}
+
+int lc_load(lc_ctx *c, const char *path) {
+    LC_CHECK_CTX(c);
+    if (!path) return fail(LC_ERR_ARG, "NULL path");
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(LC_ERR_IO, std::string("cannot open ") + path);
+    CkptHeader h;
+    bool ok = fread(&h, sizeof(h), 1, f) == 1 && !memcmp(h.magic, "LCCK", 4) && h.version == 1;
+    if (!ok || h.N != c->N) {
+        fclose(f);
+        return fail(LC_ERR_IO, "not a checkpoint of this grid size");
+    }
+    size_t n = (size_t)(c->N + 1) * (c->N + 1);
+    std::vector<double> psi(n), w(n);
+    ok = fread(psi.data(), sizeof(double), n, f) == n && fread(w.data(), sizeof(double), n, f) == n;
+    fclose(f);
+    if (!ok) return fail(LC_ERR_IO, "truncated checkpoint");
+    int rc = lc_set_state(c, psi.data(), w.data());
+    if (rc == LC_OK) c->steps = h.steps;
+    return rc;
+}
+
+}  // extern "C"

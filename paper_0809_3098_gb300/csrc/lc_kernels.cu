@@ -1,0 +1,494 @@
+// CUDA kernels of the cavity step (sm_103a).
+//
+// Method: Cardoso & Bicudo, arXiv:0809.3098.  Poisson: compact operator of
+// Sec. 3, Eq. (14), smoothed by the SOR update of Eq. (15) in colour order
+// inside a multigrid V-cycle; Thom's wall vorticity, Sec. 3.1, Eq. (25);
+// L(omega), Sec. 3, Eq. (8) with velocities from Eq. (22); SSPRK(5,4) stage
+// combination, Eqs. (9)-(13); RES monitors, Sec. 3.2, Eqs. (26)-(27).
+//
+// All stencils are bandwidth- or FP64-ALU-bound; none is a dense contraction,
+// so no tensor-core path is used.  Sums of mirror-image neighbours are always
+// paired ((E + W) + (N + S)) so that the discrete scheme stays exactly
+// equivariant under x -> 1 - x with (psi, omega, U) -> (-psi, -omega, -U).
+#include "lc_internal.h"
+
+#include <cmath>
+
+namespace lcx {
+
+namespace {
+
+constexpr int kBX = 32, kBY = 8;
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
+    int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_down_sync(0xffffffffu, r, o));
+    }
+    return r;
+}
+
+// Gauss-Seidel value at node c of the scaled operator (see lc_internal.h).
+template <typename T, int OP>
+__device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__restrict__ g, size_t c, int P) {
+    T n4 = (psi[c + 1] + psi[c - 1]) + (psi[c + P] + psi[c - P]);
+    if (OP == 1) {
+        T d4 = (psi[c + P + 1] + psi[c + P - 1]) + (psi[c - P + 1] + psi[c - P - 1]);
+        return fma(T(0.2), n4, fma(T(0.05), d4, g[c]));
+    }
+    return fma(T(0.25), n4, g[c]);
+}
+
+// ---------------------------------------------------------------------------
+// One colour phase of the SOR smoother, Eq. (15).  Compact: colour
+// (i mod 2) + 2 (j mod 2); 5-point: colour (i + j) mod 2.  Nodes of one colour
+// never neighbour each other, so the phase is a Jacobi update of that colour.
+template <typename T, int OP>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    int b = blockIdx.y * blockDim.y + threadIdx.y;
+    int i, j;
+    if (OP == 1) {
+        i = ((colour & 1) ? 1 : 2) + 2 * a;
+        j = ((colour >> 1) ? 1 : 2) + 2 * b;
+    } else {
+        j = 1 + b;
+        i = (((colour + j) & 1) ? 1 : 2) + 2 * a;
+    }
+    if (i >= N || j >= N) return;
+    size_t c = (size_t)j * P + i;
+    T v = gs_value<T, OP>(psi, g, c, P);
+    if (beta != T(1)) {
+        T old = psi[c];
+        v = fma(beta, v - old, old);
+    }
+    psi[c] = v;
+}
+
+// Residual of the fine level, full-weighted onto the coarse level; also zeroes
+// the coarse correction (its initial guess).  A 16x16 block of coarse nodes
+// needs the fine residual on a 33x33 patch, computed once into shared memory.
+constexpr int kRT = 16;
+template <typename T, int OP>
+__global__ void __launch_bounds__(kRT *kRT)
+    k_residual_restrict(const T *__restrict__ psi, const T *__restrict__ g, int Nf, int Pf, T *__restrict__ gc,
+                        T *__restrict__ psic, int Pc) {
+    __shared__ T rho[2 * kRT + 1][2 * kRT + 2];
+    int Nc = Nf / 2;
+    int I0 = 1 + blockIdx.x * kRT, J0 = 1 + blockIdx.y * kRT;
+    int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;
+    int t = threadIdx.y * kRT + threadIdx.x;
+    for (int k = t; k < (2 * kRT + 1) * (2 * kRT + 1); k += kRT * kRT) {
+        int x = k % (2 * kRT + 1), y = k / (2 * kRT + 1);
+        int i = fi0 + x, j = fj0 + y;
+        T r = T(0);
+        if (i >= 1 && i < Nf && j >= 1 && j < Nf) {
+            size_t c = (size_t)j * Pf + i;
+            r = gs_value<T, OP>(psi, g, c, Pf) - psi[c];
+        }
+        rho[y][x] = r;
+    }
+    __syncthreads();
+    int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+    if (I >= Nc || J >= Nc) return;
+    int x = 2 * threadIdx.x + 1, y = 2 * threadIdx.y + 1;
+    T e4 = (rho[y][x + 1] + rho[y][x - 1]) + (rho[y + 1][x] + rho[y - 1][x]);
+    T d4 = (rho[y + 1][x + 1] + rho[y + 1][x - 1]) + (rho[y - 1][x + 1] + rho[y - 1][x - 1]);
+    size_t cc = (size_t)J * Pc + I;
+    gc[cc] = fma(T(0.5), e4, fma(T(0.25), d4, rho[y][x]));
+    psic[cc] = T(0);
+}
+
+// Bilinear prolongation of the coarse correction, added to the fine field.
+template <typename T>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_prolong_correct(T *__restrict__ psi, int Nf, int Pf, const T *__restrict__ ec, int Pc) {
+    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= Nf || j >= Nf) return;
+    int I = i >> 1, J = j >> 1;
+    size_t cc = (size_t)J * Pc + I;
+    T e;
+    if (!(i & 1) && !(j & 1))
+        e = ec[cc];
+    else if (i & 1 && !(j & 1))
+        e = T(0.5) * (ec[cc] + ec[cc + 1]);
+    else if (!(i & 1) && (j & 1))
+        e = T(0.5) * (ec[cc] + ec[cc + Pc]);
+    else
+        e = T(0.25) * ((ec[cc] + ec[cc + 1]) + (ec[cc + Pc] + ec[cc + Pc + 1]));
+    psi[(size_t)j * Pf + i] += e;
+}
+
+// Coarsest grid (2 or 3 intervals: one or four unknowns): nsweeps colour
+// sweeps in one block.
+template <typename T, int OP>
+__global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int nsweeps, T beta) {
+    int n = N - 1;
+    int t = threadIdx.x;
+    int i = 1 + t % n, j = 1 + t / n;
+    bool active = t < n * n;
+    int my_colour = OP == 1 ? (i & 1) + 2 * (j & 1) : (i + j) & 1;
+    int ncol = OP == 1 ? 4 : 2;
+    for (int s = 0; s < nsweeps; ++s)
+        for (int colour = 0; colour < ncol; ++colour) {
+            if (active && my_colour == colour) {
+                size_t c = (size_t)j * P + i;
+                T v = gs_value<T, OP>(psi, g, c, P);
+                if (beta != T(1)) v = fma(beta, v - psi[c], psi[c]);
+                psi[c] = v;
+            }
+            __syncthreads();
+        }
+}
+
+// Per-block partial sums of rho^2 over interior nodes (FP64 accumulation).
+template <typename T, int OP>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials) {
+    __shared__ double sh[32];
+    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    double v = 0.0;
+    if (i < N && j < N) {
+        size_t c = (size_t)j * P + i;
+        double r = (double)(gs_value<T, OP>(psi, g, c, P) - psi[c]);
+        v = r * r;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+// Scaled Poisson right-hand side at the fine level from omega:
+//   compact: g = kappa h^2 B = h^2 (sum(edge omega) + 8 omega_P) / 40  (B of Eq. (17))
+//   5-point: g = h^2 omega_P / 4
+// and per-block partial sums of g^2.
+template <int OP>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_assemble_rhs(const double *__restrict__ w, double *__restrict__ g, int N, int P, double h2,
+                   double *__restrict__ gpart) {
+    __shared__ double sh[32];
+    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    double v = 0.0;
+    if (i < N && j < N) {
+        size_t c = (size_t)j * P + i;
+        double val;
+        if (OP == 1)
+            val = h2 * fma(8.0, w[c], (w[c + 1] + w[c - 1]) + (w[c + P] + w[c - P])) * (1.0 / 40.0);
+        else
+            val = 0.25 * h2 * w[c];
+        g[c] = val;
+        v = val * val;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) gpart[blockIdx.y * gridDim.x + blockIdx.x] = v;
+}
+
+// Sums the partials in a fixed order, decides whether the V-cycle loop goes on
+// and sets the while-node's condition.  Stopping rule: ||rho|| <= tol ||g||,
+// checked after every cycle; a non-finite norm or max_cycles ends the loop
+// with a status bit.
+__global__ void k_finish_norm(const double *__restrict__ rpart, int nr, const double *__restrict__ gpart, int ng,
+                              DevState *ds, cudaGraphConditionalHandle h, double tol, int max_cycles) {
+    __shared__ double sh[32];
+    double sr = 0.0, sg = 0.0;
+    for (int k = threadIdx.x; k < nr; k += blockDim.x) sr += rpart[k];
+    for (int k = threadIdx.x; k < ng; k += blockDim.x) sg += gpart[k];
+    sr = block_sum(sr, sh);
+    sg = block_sum(sg, sh);
+    if (threadIdx.x != 0) return;
+    int cyc = ds->cycles + 1;
+    double rn = sqrt(sr), gn = sqrt(sg);
+    bool finite = isfinite(rn) && isfinite(gn);
+    unsigned int more = 0;
+    if (!finite) {
+        ds->status |= kStatusNonFinite;
+    } else if (rn <= tol * gn) {
+    } else if (cyc >= max_cycles) {
+        ds->status |= kStatusNoConv;
+    } else {
+        more = 1;
+    }
+    if (more) {
+        ds->cycles = cyc;
+    } else {
+        ds->cycles = 0;
+        ds->last_cycles = cyc;
+        ds->last_rel = gn > 0.0 ? rn / gn : (rn > 0.0 ? INFINITY : 0.0);
+        ds->log[ds->nsolves % kLogN] = cyc;
+        ds->nsolves += 1;
+    }
+    cudaGraphSetConditional(h, more);
+}
+
+// Thom's wall vorticity, Eq. (25): -2 psi_adjacent / h^2 on every wall, minus
+// 2 U(x) / h on the lid; corners 0.  Written to all three vorticity buffers so
+// that every stage buffer carries the latest (lagged) walls.
+__global__ void k_thom(const double *__restrict__ psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
+                       int profile) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = N - 1;
+    double m2h2 = -2.0 * (double)N * (double)N;
+    size_t idx;
+    double val;
+    if (t < n) {
+        int i = t + 1;
+        idx = i;
+        val = m2h2 * psi[(size_t)P + i];
+    } else if (t < 2 * n) {
+        int i = t - n + 1;
+        double x = i * (1.0 / N);
+        double ui = profile == 1 ? U * 16.0 * x * x * (1.0 - x) * (1.0 - x) : U;
+        idx = (size_t)N * P + i;
+        val = m2h2 * psi[(size_t)(N - 1) * P + i] - 2.0 * ui * N;
+    } else if (t < 3 * n) {
+        int j = t - 2 * n + 1;
+        idx = (size_t)j * P;
+        val = m2h2 * psi[(size_t)j * P + 1];
+    } else if (t < 4 * n) {
+        int j = t - 3 * n + 1;
+        idx = (size_t)j * P + N;
+        val = m2h2 * psi[(size_t)j * P + N - 1];
+    } else if (t < 4 * n + 4) {
+        int k = t - 4 * n;
+        idx = (k & 1 ? (size_t)N : 0) + (k & 2 ? (size_t)N * P : 0);
+        val = 0.0;
+    } else {
+        return;
+    }
+    W0[idx] = val;
+    Wa[idx] = val;
+    Wb[idx] = val;
+}
+
+// Fused L(omega) (Eq. (8), velocities from Eq. (22)) and SSPRK(5,4) stage
+// combination (Eqs. (9)-(13)) in low-storage form (StageCoef).
+__global__ void __launch_bounds__(kBX *kBY)
+    k_rhs_stage(const double *__restrict__ psi, const double *__restrict__ in, const double *__restrict__ W0,
+                double *__restrict__ acc, double *__restrict__ out, int N, int P, double inv2h, double nu_invh2,
+                int advect, StageCoef k) {
+    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= N || j >= N) return;
+    size_t c = (size_t)j * P + i;
+    double wP = in[c], wE = in[c + 1], wW = in[c - 1], wN = in[c + P], wS = in[c - P];
+    double L = nu_invh2 * fma(-4.0, wP, (wE + wW) + (wN + wS));
+    if (advect) {
+        double u = (psi[c + P] - psi[c - P]) * inv2h;
+        double v = -(psi[c + 1] - psi[c - 1]) * inv2h;
+        double tx = u * ((wE - wW) * inv2h);
+        double ty = v * ((wN - wS) * inv2h);
+        L = (L - tx) - ty;
+    }
+    double o;
+    if (k.mode == 3) {
+        o = fma(k.bdt, L, fma(k.a1, wP, acc[c]));
+    } else {
+        o = fma(k.bdt, L, fma(k.a1, wP, k.a0 * W0[c]));
+        if (k.mode == 1) acc[c] = k.acc_in * wP;
+        else if (k.mode == 2) acc[c] = fma(k.acc_L, L, fma(k.acc_in, wP, acc[c]));
+    }
+    out[c] = o;
+}
+
+// Steady-state monitors between two states over all nodes: per-block max
+// |d omega|, sum |d psi|, sum |d omega|; the last block to finish reduces the
+// partials in block order.
+__global__ void __launch_bounds__(kBX *kBY)
+    k_monitor(const double *__restrict__ p0, const double *__restrict__ p1, const double *__restrict__ w0,
+              const double *__restrict__ w1, int N, int P, double *__restrict__ part, unsigned int *counter,
+              DevState *ds, double dt) {
+    __shared__ double sh[32];
+    __shared__ bool last;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y * blockDim.y + threadIdx.y;
+    double dw = 0.0, dp = 0.0;
+    if (i <= N && j <= N) {
+        size_t c = (size_t)j * P + i;
+        dw = fabs(w1[c] - w0[c]);
+        dp = fabs(p1[c] - p0[c]);
+    }
+    double mx = block_max(dw, sh);
+    double sw = block_sum(dw, sh);
+    double sp = block_sum(dp, sh);
+    int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        part[3 * b] = mx;
+        part[3 * b + 1] = sp;
+        part[3 * b + 2] = sw;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == (unsigned)nb - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    int t = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    double a = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int k = t; k < nb; k += nt) {
+        a = fmax(a, ((volatile double *)part)[3 * k]);
+        s1 += ((volatile double *)part)[3 * k + 1];
+        s2 += ((volatile double *)part)[3 * k + 2];
+    }
+    a = block_max(a, sh);
+    s1 = block_sum(s1, sh);
+    s2 = block_sum(s2, sh);
+    if (t == 0) {
+        ds->mon[0] = a / dt;
+        ds->mon[1] = s1 / (N + 1);
+        ds->mon[2] = s2 / (N + 1);
+        if (!isfinite(a) || !isfinite(s1) || !isfinite(s2)) ds->status |= kStatusNonFinite;
+        *counter = 0;
+    }
+}
+
+__global__ void k_zero_walls(double *psi, int N, int P) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t > N) return;
+    psi[t] = 0.0;
+    psi[(size_t)N * P + t] = 0.0;
+    psi[(size_t)t * P] = 0.0;
+    psi[(size_t)t * P + N] = 0.0;
+}
+
+inline dim3 grid2(int nx, int ny, int bx, int by) { return dim3((nx + bx - 1) / bx, (ny + by - 1) / by); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename T>
+cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int colour, T beta) {
+    dim3 blk(kBX, kBY);
+    if (op == 1) {
+        int n = N / 2;  // at most this many nodes of one parity per direction
+        k_smooth_colour<T, 1><<<grid2(n, n, kBX, kBY), blk, 0, s>>>(psi, g, N, P, colour, beta);
+    } else {
+        k_smooth_colour<T, 0><<<grid2(N / 2, N - 1, kBX, kBY), blk, 0, s>>>(psi, g, N, P, colour, beta);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_residual_restrict(cudaStream_t s, int op, const T *psi, const T *g, int Nf, int Pf, T *gc, T *psic,
+                                     int Pc) {
+    int nc = Nf / 2 - 1;
+    dim3 grid((nc + kRT - 1) / kRT, (nc + kRT - 1) / kRT), blk(kRT, kRT);
+    if (op == 1)
+        k_residual_restrict<T, 1><<<grid, blk, 0, s>>>(psi, g, Nf, Pf, gc, psic, Pc);
+    else
+        k_residual_restrict<T, 0><<<grid, blk, 0, s>>>(psi, g, Nf, Pf, gc, psic, Pc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prolong_correct(cudaStream_t s, T *psi, int Nf, int Pf, const T *ec, int Pc) {
+    k_prolong_correct<T><<<grid2(Nf - 1, Nf - 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi, Nf, Pf, ec, Pc);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta) {
+    if (op == 1)
+        k_coarsest<T, 1><<<1, 32, 0, s>>>(psi, g, N, P, nsweeps, beta);
+    else
+        k_coarsest<T, 0><<<1, 32, 0, s>>>(psi, g, N, P, nsweeps, beta);
+    return cudaGetLastError();
+}
+
+int residual_norm_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY - 1) / kBY); }
+int assemble_blocks(int N) { return residual_norm_blocks(N); }
+int monitor_blocks(int N) { return ((N + 1 + kBX - 1) / kBX) * ((N + 1 + kBY - 1) / kBY); }
+
+template <typename T>
+cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials) {
+    dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
+    if (op == 1)
+        k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials);
+    else
+        k_residual_norm<T, 0><<<grid, blk, 0, s>>>(psi, g, N, P, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, double *g, int N, int P,
+                                double *gpart) {
+    double h = 1.0 / N;
+    dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
+    if (op == 1)
+        k_assemble_rhs<1><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
+    else
+        k_assemble_rhs<0><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finish_norm(cudaStream_t s, const double *rpart, int nr, const double *gpart, int ng, DevState *ds,
+                               cudaGraphConditionalHandle h, double tol, int max_cycles) {
+    k_finish_norm<<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thom(cudaStream_t s, const double *psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
+                        int profile) {
+    int n = 4 * (N - 1) + 4;
+    k_thom<<<(n + 255) / 256, 256, 0, s>>>(psi, W0, Wa, Wb, N, P, U, profile);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rhs_stage(cudaStream_t s, const double *psi, const double *in, const double *W0, double *acc,
+                             double *out, int N, int P, double Re, int advect, StageCoef c) {
+    double inv2h = 0.5 * N;
+    double nu_invh2 = (double)N * (double)N / Re;
+    k_rhs_stage<<<grid2(N - 1, N - 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi, in, W0, acc, out, N, P, inv2h,
+                                                                         nu_invh2, advect, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi1, const double *w0,
+                           const double *w1, int N, int P, double *part, DevState *ds, double dt) {
+    // the block counter lives just past the partials
+    unsigned int *counter = reinterpret_cast<unsigned int *>(part + 3 * monitor_blocks(N));
+    k_monitor<<<grid2(N + 1, N + 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi0, psi1, w0, w1, N, P, part, counter, ds,
+                                                                       dt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P) {
+    k_zero_walls<<<(N + 1 + 255) / 256, 256, 0, s>>>(psi, N, P);
+    return cudaGetLastError();
+}
+
+#define LCX_INSTANTIATE(T)                                                                                           \
+    template cudaError_t launch_smooth_colour<T>(cudaStream_t, int, T *, const T *, int, int, int, T);               \
+    template cudaError_t launch_residual_restrict<T>(cudaStream_t, int, const T *, const T *, int, int, T *, T *,    \
+                                                     int);                                                           \
+    template cudaError_t launch_prolong_correct<T>(cudaStream_t, T *, int, int, const T *, int);                     \
+    template cudaError_t launch_coarsest<T>(cudaStream_t, int, T *, const T *, int, int, int, T);                    \
+    template cudaError_t launch_residual_norm<T>(cudaStream_t, int, const T *, const T *, int, int, double *);
+LCX_INSTANTIATE(double)
+LCX_INSTANTIATE(float)
+
+}  // namespace lcx

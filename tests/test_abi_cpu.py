@@ -1,0 +1,85 @@
+"""The C ABI library loads without a GPU, exports every function that
+include/*.h declares, and validates its arguments on the host."""
+import ctypes
+import glob
+import math
+import os
+import re
+
+import pytest
+
+from paper_0809_3098_gb300 import lc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(lc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_0809_3098_gb300 import build
+
+    build.build()
+    return lc.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for required in ("lc_create", "lc_step", "lc_get_psi", "lc_get_omega", "lc_residual", "lc_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    raw = ctypes.CDLL(lc.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_create_validates_arguments(L):
+    assert not L.lc_create(20, 100.0, 0.0, 1e-10)      # 20 = 4 * 5
+    assert "N must be" in lc.last_error()
+    assert not L.lc_create(16, -5.0, 0.0, 1e-10)
+    assert not L.lc_create(16, 100.0, 0.0, 0.0)
+    assert not L.lc_create(4, 100.0, 0.0, 1e-10)
+
+
+def test_dt_rule_and_params(L):
+    h = lc.lc_create(1024, 10000.0, 0.0, 1e-10)
+    p = lc.lc_get_params(h)
+    assert p[2] == 0.25 * min(1 / 1024, 10000.0 / 1024**2 / 4)
+    assert p[5] == 10  # 1024 .. 2
+    lc.lc_destroy(h)
+    h = lc.lc_create(384, 1000.0, 1e-3, 1e-10)
+    p = lc.lc_get_params(h)
+    assert p[2] == 1e-3 and p[5] == 8  # 384 .. 3
+    lc.lc_destroy(h)
+
+
+def test_options_validate_without_gpu(L):
+    h = lc.lc_create(64, 1000.0, 0.0, 1e-10)
+    assert lc.lc_set_option(h, "nu1", 3) == lc.LC_OK
+    assert lc.lc_set_option(h, "nu1", 0) == lc.LC_ERR_ARG
+    assert lc.lc_set_option(h, "beta", 2.0) == lc.LC_ERR_ARG
+    assert lc.lc_set_option(h, "op", 0) == lc.LC_OK
+    assert lc.lc_set_option(h, "op", 2) == lc.LC_ERR_ARG
+    assert lc.lc_set_option(h, "nonsense", 1) == lc.LC_ERR_ARG
+    assert "unknown option" in lc.last_error()
+    lc.lc_destroy(h)
+    assert lc.lc_set_option(h, "nu1", 2) == lc.LC_ERR_ARG  # destroyed
+    assert lc.lc_step(0, 1) == lc.LC_ERR_ARG
+    assert math.isnan(lc.lc_residual(0))
+
+
+def test_workspace_bytes(L):
+    assert lc.lc_workspace_bytes(20, 0) == 0
+    a, b = lc.lc_workspace_bytes(512, 0), lc.lc_workspace_bytes(1024, 0)
+    assert 3.5 < b / a < 4.5
+    assert b % 256 == 0

@@ -1,0 +1,209 @@
+"""GPU parity: the CUDA library (through the C ABI) against the CPU oracle.
+
+Both sides run the same algorithm (same operator, colour order, V-cycle and
+stopping rule), so they agree to rounding and make the same number of V-cycles
+per solve; the bar for the FP64 path is 1e-10 relative (max-norm over all
+nodes, relative to the reference's max), and the cycle logs must be equal.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0809_3098_gb300 import lc
+from paper_0809_3098_gb300.workloads import dt_rule, smooth_random_state
+
+pytestmark = pytest.mark.gpu
+
+OPS = {"5pt": lc.LC_OP_5PT, "compact": lc.LC_OP_COMPACT}
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def pair(N, Re, op, tol=1e-10, **opts):
+    dt = dt_rule(N, Re)
+    g = lc.Cavity(N, Re, dt, tol, op=op, **opts)
+    opts.pop("monitor", None)  # the oracle computes monitors by a separate call
+    r = oracle.Cavity(N, Re, dt, tol, op=op, **opts)
+    return g, r
+
+
+@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 96])
+@pytest.mark.parametrize("opname", ["5pt", "compact"])
+def test_small_grids_match_oracle(N, opname):
+    g, r = pair(N, 400.0, OPS[opname])
+    g.step(4)
+    assert r.step(4) == oracle.OK
+    assert rel(g.psi(), r.psi()) < 1e-12
+    assert rel(g.omega(), r.omega()) < 1e-12
+    assert np.array_equal(g.cycle_log(), r.cycle_log())
+
+
+def test_rest_state():
+    N = 64
+    g = lc.Cavity(N, 1000.0)
+    w = g.omega()
+    assert not g.psi().any()
+    assert np.all(w[N, 1:N] == -2.0 * N) and not w[:N].any() and w[N, 0] == 0 and w[N, N] == 0
+
+
+def test_config_128_re1000_100_steps():
+    """Lid-driven cavity, 128x128, Re 1000, dt rule, tol 1e-10, 100 steps, FP64."""
+    N, Re, steps = 128, 1000.0, 100
+    g, r = pair(N, Re, lc.LC_OP_COMPACT)
+    g.step(steps)
+    assert r.step(steps) == oracle.OK
+    ep, ew = rel(g.psi(), r.psi()), rel(g.omega(), r.omega())
+    assert ep <= 1e-10 and ew <= 1e-10, (ep, ew)
+    gl, rl = g.cycle_log(), r.cycle_log()
+    assert len(gl) == 5 * steps
+    assert np.array_equal(gl, rl)
+    assert g.residual() <= 1e-10
+
+
+@pytest.mark.parametrize("opname", ["5pt", "compact"])
+def test_options_match_oracle(opname):
+    N = 64
+    g, r = pair(N, 2000.0, OPS[opname], nu1=1, nu2=3, beta=1.15, nuc=8)
+    g.step(3)
+    r.step(3)
+    assert rel(g.psi(), r.psi()) < 1e-12 and rel(g.omega(), r.omega()) < 1e-12
+    assert np.array_equal(g.cycle_log(), r.cycle_log())
+
+
+def test_regularised_lid_stokes_limit():
+    N = 64
+    g, r = pair(N, 50.0, lc.LC_OP_COMPACT, profile=1, advect=0)
+    g.step(5)
+    r.step(5)
+    assert rel(g.psi(), r.psi()) < 1e-12 and rel(g.omega(), r.omega()) < 1e-12
+    p = g.psi()
+    assert np.array_equal(p, p[:, ::-1])  # Stokes limit: mirror-symmetric, bit for bit
+
+
+@pytest.mark.parametrize("N", [64, 1024])
+def test_lid_reversal_equivariance_bitwise(N):
+    """Mirror-paired sums make the GPU scheme exactly equivariant under
+    x -> 1 - x, (psi, omega, U) -> (-psi, -omega, -U), at any size."""
+    Re = 10000.0
+    a = lc.Cavity(N, Re)
+    b = lc.Cavity(N, Re, U=-1.0)
+    a.step(3)
+    b.step(3)
+    pa, pb = a.psi(), b.psi()
+    assert np.abs(pa).max() > 0
+    assert np.array_equal(pb, -pa[:, ::-1])
+    assert np.array_equal(b.omega(), -a.omega()[:, ::-1])
+
+
+def test_set_state_then_step_matches_oracle():
+    N = 96
+    psi, omega = smooth_random_state(N, seed=7)
+    g, r = pair(N, 3000.0, lc.LC_OP_COMPACT)
+    g.set_state(psi, omega)
+    r.set_state(psi, omega)
+    # Thom walls agree to rounding (-2 N^2 psi on the GPU, -2 psi / h^2 in the oracle)
+    assert rel(g.omega(), r.omega()) < 1e-14
+    g.step(2)
+    r.step(2)
+    assert rel(g.psi(), r.psi()) < 1e-12 and rel(g.omega(), r.omega()) < 1e-12
+    assert np.array_equal(g.cycle_log(), r.cycle_log())
+
+
+def test_monitors_match_oracle():
+    N, Re = 64, 1000.0
+    g, r = pair(N, Re, lc.LC_OP_COMPACT, monitor=1)
+    g.step(3)
+    r.step(2)
+    p0, w0 = r.psi(), r.omega()
+    r.step(1)
+    ref = oracle.monitors(N, dt_rule(N, Re), p0, r.psi(), w0, r.omega())
+    out = g.monitor()
+    assert np.allclose(out[:3], ref, rtol=1e-9, atol=0)
+    assert out[3] == r.cycle_log()[-1]
+
+
+def test_checkpoint_roundtrip(tmp_path):
+    N = 32
+    a = lc.Cavity(N, 500.0)
+    a.step(3)
+    path = str(tmp_path / "ck.bin")
+    a.save(path)
+    b = lc.Cavity(N, 500.0)
+    b.load(path)
+    assert b.params["steps"] == 3
+    assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
+
+
+def test_library_workspace_and_own_stream():
+    N = 32
+    a = lc.Cavity(N, 500.0, workspace="library")
+    b = lc.Cavity(N, 500.0)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.psi(), b.psi())
+
+
+def test_nonfinite_state_reports_error():
+    N = 16
+    g = lc.Cavity(N, 100.0)
+    psi, omega = np.zeros((N + 1, N + 1)), np.zeros((N + 1, N + 1))
+    omega[5, 5] = np.nan
+    g.set_state(psi, omega)
+    g.step(1)
+    with pytest.raises(lc.LCError) as e:
+        g.synchronize()
+    assert e.value.code == lc.LC_ERR_NONFINITE
+
+
+def test_max_cycles_reports_noconv():
+    g = lc.Cavity(64, 1000.0, max_cycles=1, tol=1e-14)
+    g.step(1)
+    with pytest.raises(lc.LCError) as e:
+        g.synchronize()
+    assert e.value.code == lc.LC_ERR_NOCONV
+    g.synchronize()  # the status is cleared once reported
+
+
+def test_invalid_arguments():
+    with pytest.raises(lc.LCError):
+        lc.Cavity(20, 100.0)
+    g = lc.Cavity(16, 100.0)
+    with pytest.raises(lc.LCError):
+        g.set_option("nu1", 0)
+    with pytest.raises(lc.LCError):
+        g.set_option("beta", 2.5)
+    small = np.zeros(10)
+    assert lc.lc_get_psi(g.handle, small) == lc.LC_ERR_SIZE
+    g.step(1)
+    with pytest.raises(lc.LCError):
+        g.set_option("op", 0)  # layout options only before first use
+    h = g.handle
+    g.close()
+    assert lc.lc_step(h, 1) == lc.LC_ERR_ARG
+
+
+def test_runs_on_torch_stream_in_order():
+    """Work is enqueued on torch's current stream, so torch events bracket it."""
+    import torch
+
+    g = lc.Cavity(256, 1000.0)
+    g.step(1)
+    g.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    g.step(3)
+    e1.record(s)
+    e1.synchronize()
+    assert e0.elapsed_time(e1) > 0.05  # three steps of ~25 V-cycles cannot take < 50 us
+    a = torch.zeros(1, device="cuda")
+    with torch.cuda.stream(torch.cuda.Stream()):
+        h = lc.Cavity(64, 100.0)  # binds the side stream
+        h.step(2)
+        h.synchronize()
+    assert g.params["steps"] == 4
