@@ -186,6 +186,35 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * change the state: use only on a context whose state no longer matters. */
 int lc_bench_kernel(lc_ctx *ctx, int kernel, int reps, double out[4]);
 
+/* Largest N accepted by lc_monitor_noalloc: the size of its fixed scratch. */
+#define LC_NOALLOC_MAX_N 8192
+
+/* Steady-state monitors of two caller-owned device states, without allocating.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot call cudaMalloc (a host framework that owns all device memory
+ * through its own pool, work enqueued while a CUDA graph is being captured,
+ * a process with a fixed memory budget).  It computes what lc_monitor's
+ * out[0..2] report: out[0] = max |omega1 - omega0| / dt, out[1] = RES_psi,
+ * out[2] = RES_omega (Eqs. (26)-(27), 1/N read as 1/(N+1)), over all
+ * (N+1) x (N+1) nodes.
+ *   psi0, psi1, omega0, omega1: device FP64 arrays of N+1 rows, element (i, j)
+ *     at j*pitch + i (pitch >= N+1; pitch = N+1 is the host layout above);
+ *     read only.  out: device pointer to 3 doubles, written.
+ *   cuda_stream: the work is enqueued there (NULL = legacy default stream)
+ *     and the call returns without waiting.
+ * Its scratch (one partial per row and a block counter) is a file-scope
+ * device array of about 192 KiB, sized for N <= LC_NOALLOC_MAX_N, that every
+ * GPU loading the library holds until the process exits.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make the first call on each device before any
+ * stream capture.  No call allocates or frees memory.  All calls share the
+ * array: calls that overlap on the GPU (two streams, two threads) race;
+ * calls in order on one stream are safe.  Returns LC_ERR_SIZE for
+ * N > LC_NOALLOC_MAX_N, LC_ERR_ARG for NULL arrays, pitch < N+1, N < 1 or
+ * dt <= 0, LC_ERR_CUDA if the set-up or the launch fails. */
+int lc_monitor_noalloc(int N, const double *psi0, const double *psi1, const double *omega0,
+                       const double *omega1, size_t pitch, double dt, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

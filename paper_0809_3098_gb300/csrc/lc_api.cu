@@ -118,6 +118,8 @@ bool make_layout(int N, int precision, Layout &L) {
 
 }  // namespace
 
+void lcx::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
 struct lc_ctx {
     int N;
     double Re, dt, tol;

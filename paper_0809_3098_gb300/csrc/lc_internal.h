@@ -81,4 +81,7 @@ cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi
                            int N, int P, double *part, DevState *ds, double dt);
 cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P);
 
+// Sets the calling thread's lc_last_error() message.
+void set_last_error(const char *msg);
+
 }  // namespace lcx

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
         "lc_get_params": ([vp, _dp], ci),
         "lc_launch_stats": ([vp, _dp], ci),
         "lc_bench_kernel": ([vp, ci, ci, _dp], ci),
+        "lc_monitor_noalloc": ([ci, vp, vp, vp, vp, sz, cd, vp, vp], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -186,6 +187,16 @@ def lc_bench_kernel(ctx: int, kernel: int, reps: int) -> np.ndarray:
     out = np.zeros(4)
     _check(lib().lc_bench_kernel(ctx, kernel, reps, _p(out)), "lc_bench_kernel")
     return out
+
+
+LC_NOALLOC_MAX_N = 8192
+
+
+def lc_monitor_noalloc(N: int, psi0_ptr: int, psi1_ptr: int, omega0_ptr: int, omega1_ptr: int, pitch: int,
+                       dt: float, out_ptr: int, stream_handle: int = 0) -> int:
+    """Monitors of two device states without any allocation (device pointers in and out)."""
+    return lib().lc_monitor_noalloc(N, psi0_ptr, psi1_ptr, omega0_ptr, omega1_ptr, pitch, dt, out_ptr,
+                                    stream_handle)
 
 
 # Convenience object ---------------------------------------------------------
