@@ -117,6 +117,12 @@ const char *lc_last_error(void);
  *   "advect"      1 (default), 0 drops the transport terms of Eq. (8)
  *   "monitor"     1 computes lc_monitor's values over the last step of each
  *                 lc_step call (default 0)
+ *   "graph"       1 (default) replays each step as one CUDA graph whose
+ *                 V-cycle loops are device-side while-nodes; 0 launches the
+ *                 same kernels one by one and drives the V-cycle loop from the
+ *                 host (one stream sync per cycle; for per-kernel profiling,
+ *                 since kernels in graphs with conditional nodes cannot be
+ *                 profiled)
  * Returns LC_ERR_ARG for an unknown key or a value out of range. */
 int lc_set_option(lc_ctx *ctx, const char *key, double value);
 
@@ -177,9 +183,13 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
 
 /* Roofline diagnostics: times `reps` >= 1 back-to-back launches of one kernel
  * of the step, with the arguments it has inside the step, between CUDA events
- * on the context stream.  kernel 0 = fine-level smoother colour phase (the
- * colours taken in turn), 1 = fused L(omega) + stage combination (stage 2),
- * 2 = fine-level residual + full-weighting restriction.  out[0] = mean ms per
+ * on the context stream.  FP64 precision: kernel 0 = fine-level smoother
+ * colour phase (the colours taken in turn), 1 = fused L(omega) + stage
+ * combination (stage 2), 2 = fine-level residual + full-weighting
+ * restriction.  Mixed precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
+ * residual, restriction), 1 = FP32 L(omega) + FP64 stage combination (stage
+ * 2), 2 = FP64 residual rounded to FP32, 3 = fine-level FP32 tile kernel
+ * (prolongation, post-smoothing, FP64 psi += e).  out[0] = mean ms per
  * launch, out[1] = algorithmic bytes per launch (each array element the
  * kernel must read or write, counted once), out[2] = FP64 and out[3] = FP32
  * floating-point operations per launch (an FMA counts two).  The launches

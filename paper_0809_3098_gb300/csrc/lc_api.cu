@@ -71,20 +71,28 @@ int level_count(int N) {
 
 bool valid_N(int N) { return N >= 8 && N <= 8192 && level_count(N) >= 2; }
 
-// Offsets of every device array inside one workspace block.
+// Offsets of every device array inside one workspace block.  FP64 arrays of
+// level l have N_l + 1 rows of pitch Pl[l] elements; FP32 arrays use the same
+// pitch in elements.
 struct Layout {
-    int nlev = 0;
+    int nlev = 0, precision = 0;
     int Nl[kMaxLevels], Pl[kMaxLevels];
-    size_t psi[kMaxLevels], g[kMaxLevels];
+    size_t psi[kMaxLevels], psiB[kMaxLevels], g[kMaxLevels];  // FP64 (mixed: level 0 only)
+    size_t eA[kMaxLevels], eB[kMaxLevels], g32[kMaxLevels];   // FP32 correction hierarchy (mixed)
+    size_t psi32, r32;                                         // FP32 shadow of psi, FP32 residual (mixed)
     size_t W0, Wa, Wb, ACC, snap_psi, snap_w;
+    size_t W0s, Was, Wbs;                                      // FP32 shadows of W0, Wa, Wb (mixed)
     size_t rpart, gpart, mpart, ds;
-    int nrpart, ngpart, nmpart;
+    int nrpart, nrpart_grid, ngpart, nmpart;
     size_t total = 0;
 };
 
 bool make_layout(int N, int precision, Layout &L) {
     if (!valid_N(N) || (precision != LC_PREC_FP64 && precision != LC_PREC_MIXED)) return false;
+    L = Layout();
     L.nlev = level_count(N);
+    L.precision = precision;
+    bool mixed = precision == LC_PREC_MIXED;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -95,17 +103,33 @@ bool make_layout(int N, int precision, Layout &L) {
         L.Nl[l] = N >> l;
         L.Pl[l] = pitch_of(L.Nl[l]);
         size_t n = (size_t)(L.Nl[l] + 1) * L.Pl[l];
-        L.psi[l] = take(n * sizeof(double));
-        L.g[l] = take(n * sizeof(double));
+        if (!mixed || l == 0) {
+            L.psi[l] = take(n * sizeof(double));
+            L.g[l] = take(n * sizeof(double));
+        }
+        if (!mixed) L.psiB[l] = take(n * sizeof(double));
+        if (mixed) {
+            L.eA[l] = take(n * sizeof(float));
+            L.eB[l] = take(n * sizeof(float));
+            if (l > 0) L.g32[l] = take(n * sizeof(float));
+        }
     }
-    size_t n0 = (size_t)(N + 1) * L.Pl[0] * sizeof(double);
-    L.W0 = take(n0);
-    L.Wa = take(n0);
-    L.Wb = take(n0);
-    L.ACC = take(n0);
-    L.snap_psi = take(n0);
-    L.snap_w = take(n0);
-    L.nrpart = residual_norm_blocks(N);
+    size_t n0 = (size_t)(N + 1) * L.Pl[0];
+    if (mixed) {
+        L.psi32 = take(n0 * sizeof(float));
+        L.r32 = take(n0 * sizeof(float));
+        L.W0s = take(n0 * sizeof(float));
+        L.Was = take(n0 * sizeof(float));
+        L.Wbs = take(n0 * sizeof(float));
+    }
+    L.W0 = take(n0 * sizeof(double));
+    L.Wa = take(n0 * sizeof(double));
+    L.Wb = take(n0 * sizeof(double));
+    L.ACC = take(n0 * sizeof(double));
+    L.snap_psi = take(n0 * sizeof(double));
+    L.snap_w = take(n0 * sizeof(double));
+    L.nrpart_grid = residual_norm_blocks(N);
+    L.nrpart = L.nrpart_grid > tiles_of(N) ? L.nrpart_grid : tiles_of(N);
     L.ngpart = assemble_blocks(N);
     L.nmpart = monitor_blocks(N);
     L.rpart = take(L.nrpart * sizeof(double));
@@ -125,7 +149,9 @@ struct lc_ctx {
     double Re, dt, tol;
     int op = LC_OP_COMPACT, precision = LC_PREC_FP64;
     int nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
+    int use_graph = 1;
     double beta = 1.0, U = 1.0;
+    int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
 
     Layout lay;
     char *ws = nullptr;
@@ -151,6 +177,11 @@ struct lc_ctx {
     }
     double *psi(int l) const { return at<double>(lay.psi[l]); }
     double *g(int l) const { return at<double>(lay.g[l]); }
+    double *psiB(int l) const { return at<double>(lay.psiB[l]); }
+    float *eA(int l) const { return at<float>(lay.eA[l]); }
+    float *eB(int l) const { return at<float>(lay.eB[l]); }
+    float *g32(int l) const { return l == 0 ? at<float>(lay.r32) : at<float>(lay.g32[l]); }
+    bool mixed() const { return precision == LC_PREC_MIXED; }
     DevState *ds() const { return at<DevState>(lay.ds); }
 };
 
@@ -174,11 +205,34 @@ void release_graph(lc_ctx *c) {
     c->graph_dirty = true;
 }
 
-// Enqueues one V-cycle (FP64) on stream s.
-int enqueue_vcycle(lc_ctx *c, cudaStream_t s) {
+// First level handled by the one-block coarse V-cycle (N_l <= coarse_max and
+// small enough for shared memory).
+int coarse_level(const lc_ctx *c) {
+    const Layout &L = c->lay;
+    int elem = c->mixed() ? 4 : 8;
+    int cmax = c->coarse_max > 0 ? c->coarse_max : (c->mixed() ? 64 : 32);
+    for (int l = 0; l < L.nlev; ++l)
+        if (L.Nl[l] <= cmax && coarse_smem_bytes(L.Nl[l], L.nlev - l, elem) <= kMaxSmem - 1024) return l;
+    return L.nlev - 1;
+}
+
+// Whether the shared-memory tile kernels can run every level above the
+// coarse level with the current smoothing counts.
+bool blocked_ok(const lc_ctx *c) {
+    if (!c->blocked && !c->mixed()) return false;
+    int lc = coarse_level(c);
+    int nu = c->nu1 > c->nu2 ? c->nu1 : c->nu2;
+    for (int l = 0; l < lc; ++l)
+        if (tile_smem_bytes(c->lay.Nl[l], c->op, nu, c->mixed() ? 4 : 8) > kMaxSmem - 1024) return false;
+    return true;
+}
+
+// One V-cycle with one launch per colour phase on every level (the plain
+// form; used when blocked = 0 or the tiles would not fit in shared memory).
+int enqueue_vcycle_phases(lc_ctx *c, cudaStream_t s) {
     const Layout &L = c->lay;
     int nc = c->op == LC_OP_COMPACT ? 4 : 2;
-    c->kernels_per_cycle = (L.nlev - 1) * ((c->nu1 + c->nu2) * nc + 2) + 1 + 2;  // + coarsest, norm, finisher
+    c->kernels_per_cycle = (L.nlev - 1) * ((c->nu1 + c->nu2) * nc + 2) + 1;
     for (int l = 0; l + 1 < L.nlev; ++l) {
         for (int sw = 0; sw < c->nu1; ++sw)
             for (int col = 0; col < nc; ++col)
@@ -197,17 +251,172 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s) {
     return LC_OK;
 }
 
-// Captures: right-hand side of omega_buf, the V-cycle while-loop, Thom.
-int capture_solve(lc_ctx *c, cudaStream_t s, double *omega_buf) {
+// Enqueues one FP64 V-cycle on stream s.  Sets *norm_done when the cycle's
+// last kernel already wrote the fine-level residual partials.
+int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done) {
+    *norm_done = false;
+    if (!blocked_ok(c)) return enqueue_vcycle_phases(c, s);
+    const Layout &L = c->lay;
+    int nc = c->op == LC_OP_COMPACT ? 4 : 2;
+    int lc = coarse_level(c);
+    bool phases0 = c->fine_phases && lc > 0;
+    double *rpart = c->at<double>(L.rpart);
+    int k = 0;
+    for (int l = 0; l < lc; ++l) {
+        if (l == 0 && phases0) {
+            for (int sw = 0; sw < c->nu1; ++sw)
+                for (int col = 0; col < nc; ++col, ++k)
+                    LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta));
+            LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], c->g(1),
+                                                     c->psi(1), L.Pl[1]));
+        } else {
+            LC_CUDA(launch_down<double>(s, c->op, c->psi(l), l > 0, c->g(l), c->psiB(l), L.Nl[l], L.Pl[l], c->g(l + 1),
+                                        L.Pl[l + 1], c->nu1, c->beta));
+        }
+        ++k;
+    }
+    LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], lc == 0 ? c->psi(0) : nullptr, c->psi(lc), L.Pl[lc],
+                                  L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, lc == 0 ? rpart : nullptr));
+    ++k;
+    Correct64 none{nullptr, 0, nullptr, 0};
+    for (int l = lc - 1; l >= 0; --l) {
+        if (l == 0 && phases0) {
+            LC_CUDA(launch_prolong_correct<double>(s, c->psi(0), L.Nl[0], L.Pl[0], c->psi(1), L.Pl[1]));
+            for (int sw = 0; sw < c->nu2; ++sw)
+                for (int col = 0; col < nc; ++col, ++k)
+                    LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta));
+        } else {
+            LC_CUDA(launch_up<double>(s, c->op, c->psiB(l), c->g(l), c->psi(l + 1), L.Pl[l + 1], c->psi(l), L.Nl[l],
+                                      L.Pl[l], c->nu2, c->beta, l == 0 ? rpart : nullptr, none));
+        }
+        ++k;
+    }
+    *norm_done = lc == 0 || !phases0;
+    c->kernels_per_cycle = k;
+    return LC_OK;
+}
+
+// Enqueues one mixed-precision refinement step: an FP32 V-cycle for the
+// correction e of L_h e = r (r = the FP64 residual rounded to FP32, starting
+// from e = 0), psi64 += e on the fine level, then the new FP64 residual with
+// its norm partials (which also becomes the next step's r).
+int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s) {
+    const Layout &L = c->lay;
+    int lc = coarse_level(c);
+    float beta = (float)c->beta;
+    int k = 0;
+    for (int l = 0; l < lc; ++l, ++k)
+        LC_CUDA(launch_down<float>(s, c->op, nullptr, 1, c->g32(l), c->eB(l), L.Nl[l], L.Pl[l], c->g32(l + 1),
+                                   L.Pl[l + 1], c->nu1, beta));
+    LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc], L.nlev - lc,
+                                 c->nu1, c->nu2, c->nuc, beta, nullptr));
+    ++k;
+    float *psi32 = c->at<float>(L.psi32);
+    if (lc == 0) {
+        LC_CUDA(launch_correct64(s, c->eA(0), L.Pl[0], c->psi(0), L.Pl[0], psi32, L.Pl[0], c->N));
+        ++k;
+    }
+    for (int l = lc - 1; l >= 0; --l, ++k) {
+        Correct64 cor{nullptr, 0, nullptr, 0};
+        if (l == 0) cor = Correct64{c->psi(0), L.Pl[0], psi32, L.Pl[0]};
+        LC_CUDA(launch_up<float>(s, c->op, c->eB(l), c->g32(l), c->eA(l + 1), L.Pl[l + 1], c->eA(l), L.Nl[l], L.Pl[l],
+                                 c->nu2, beta, nullptr, cor));
+    }
+    LC_CUDA(launch_residual64_to32(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<float>(L.r32), L.Pl[0],
+                                   c->at<double>(L.rpart)));
+    c->kernels_per_cycle = k + 1;
+    return LC_OK;
+}
+
+// Body of one iteration of a Poisson loop: a cycle, the residual norm and the
+// finisher (h != 0: sets the graph while-node's condition; h == 0: eager).
+int enqueue_cycle_body(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
+    const Layout &L = c->lay;
+    double *rpart = c->at<double>(L.rpart);
+    int nparts;
+    if (c->mixed()) {
+        int rc = enqueue_vcycle_mixed(c, s);
+        if (rc) return rc;
+        nparts = L.nrpart_grid;
+    } else {
+        bool norm_done = false;
+        int rc = enqueue_vcycle(c, s, &norm_done);
+        if (rc) return rc;
+        if (!norm_done) {
+            LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], rpart));
+            c->kernels_per_cycle += 1;
+            nparts = L.nrpart_grid;
+        } else {
+            nparts = coarse_level(c) == 0 ? 1 : tiles_of(c->N);
+        }
+    }
+    LC_CUDA(launch_finish_norm(s, rpart, nparts, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol,
+                               c->max_cycles));
+    c->kernels_per_cycle += 1;
+    return LC_OK;
+}
+
+// The five stages of one step, each: the fused L(omega) + stage combination,
+// then a Poisson solve for the new stage vorticity.
+struct StagePlan {
+    double *in64, *out64;
+    float *in32, *out32;
+    StageCoef k;
+};
+
+void stage_plan(const lc_ctx *c, StagePlan st[5]) {
+    const Layout &L = c->lay;
+    double *W0 = c->at<double>(L.W0), *Wa = c->at<double>(L.Wa), *Wb = c->at<double>(L.Wb);
+    float *W0s = c->mixed() ? c->at<float>(L.W0s) : nullptr, *Was = c->mixed() ? c->at<float>(L.Was) : nullptr,
+          *Wbs = c->mixed() ? c->at<float>(L.Wbs) : nullptr;
+    double dt = c->dt;
+    st[0] = {W0, Wa, W0s, Was, StageCoef{1.0, 0.0, B10 * dt, 0.0, 0.0, 0}};
+    st[1] = {Wa, Wb, Was, Wbs, StageCoef{A20, A21, B21 * dt, 0.0, 0.0, 0}};
+    st[2] = {Wb, Wa, Wbs, Was, StageCoef{A30, A32, B32 * dt, A52, 0.0, 1}};
+    st[3] = {Wa, Wb, Was, Wbs, StageCoef{A40, A43, B43 * dt, A53, B53 * dt, 2}};
+    st[4] = {Wb, W0, Wbs, W0s, StageCoef{0.0, A54, B54 * dt, 0.0, 0.0, 3}};
+}
+
+int enqueue_thom(lc_ctx *c, cudaStream_t s) {
+    const Layout &L = c->lay;
+    if (c->mixed()) {
+        double *w64[3] = {c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb)};
+        float *w32[3] = {c->at<float>(L.W0s), c->at<float>(L.Was), c->at<float>(L.Wbs)};
+        LC_CUDA(launch_thom_mixed(s, c->psi(0), w64, w32, c->N, L.Pl[0], L.Pl[0], c->U, c->profile));
+    } else {
+        LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), c->N,
+                            L.Pl[0], c->U, c->profile));
+    }
+    return LC_OK;
+}
+
+// Everything of stage k before its Poisson loop.
+int enqueue_stage_head(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
     const Layout &L = c->lay;
     int N = c->N, P = L.Pl[0];
-    LC_CUDA(launch_assemble_rhs(s, c->op, omega_buf, c->g(0), N, P, c->at<double>(L.gpart)));
+    if (c->mixed()) {
+        LC_CUDA(launch_rhs_stage_mixed(s, c->at<float>(L.psi32), P, st.in32, st.in64, c->at<double>(L.W0),
+                                       c->at<double>(L.ACC), st.out64, st.out32, N, P, P, c->Re, c->advect, st.k));
+        LC_CUDA(launch_assemble_rhs(s, c->op, st.out64, c->g(0), N, P, c->at<double>(L.gpart)));
+        LC_CUDA(launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
+                                       c->at<double>(L.rpart)));
+    } else {
+        LC_CUDA(launch_rhs_stage(s, c->psi(0), st.in64, c->at<double>(L.W0), c->at<double>(L.ACC), st.out64, N, P,
+                                 c->Re, c->advect, st.k));
+        LC_CUDA(launch_assemble_rhs(s, c->op, st.out64, c->g(0), N, P, c->at<double>(L.gpart)));
+    }
+    return LC_OK;
+}
 
-    cudaStreamCaptureStatus st;
+// Captures one stage: head, the Poisson while-loop, Thom.
+int capture_stage(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
+    int rc = enqueue_stage_head(c, s, st);
+    if (rc) return rc;
+    cudaStreamCaptureStatus cst;
     cudaGraph_t g;
     const cudaGraphNode_t *deps = nullptr;
     size_t ndeps = 0;
-    LC_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &g, &deps, nullptr, &ndeps));
+    LC_CUDA(cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps));
     cudaGraphConditionalHandle h;
     LC_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
     cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
@@ -221,42 +430,42 @@ int capture_solve(lc_ctx *c, cudaStream_t s, double *omega_buf) {
     LC_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
 
     LC_CUDA(cudaStreamBeginCaptureToGraph(c->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_vcycle(c, c->cap2);
-    if (rc == LC_OK) {
-        cudaError_t e = launch_residual_norm<double>(c->cap2, c->op, c->psi(0), c->g(0), N, P, c->at<double>(L.rpart));
-        if (e == cudaSuccess)
-            e = launch_finish_norm(c->cap2, c->at<double>(L.rpart), L.nrpart, c->at<double>(L.gpart), L.ngpart,
-                                   c->ds(), h, c->tol, c->max_cycles);
-        if (e != cudaSuccess) rc = cuda_fail(e, "body launch");
-    }
+    rc = enqueue_cycle_body(c, c->cap2, h);
     cudaGraph_t tmp = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(c->cap2, &tmp);
     if (rc != LC_OK) return rc;
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture(body)");
+    return enqueue_thom(c, s);
+}
 
-    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), N, P, c->U,
-                        c->profile));
+// Eager mode: the same kernels launched one by one, the V-cycle loop driven
+// from the host (one stream sync per cycle).  Used for per-kernel profiling:
+// kernels inside a graph with conditional nodes cannot be profiled.
+int eager_step(lc_ctx *c) {
+    cudaStream_t s = c->stream();
+    StagePlan st[5];
+    stage_plan(c, st);
+    for (int k = 0; k < 5; ++k) {
+        int rc = enqueue_stage_head(c, s, st[k]);
+        if (rc) return rc;
+        for (;;) {
+            rc = enqueue_cycle_body(c, s, 0);
+            if (rc) return rc;
+            int more = 0;
+            LC_CUDA(cudaMemcpyAsync(&more, &c->ds()->more, sizeof(int), cudaMemcpyDeviceToHost, s));
+            LC_CUDA(cudaStreamSynchronize(s));
+            if (!more) break;
+        }
+        rc = enqueue_thom(c, s);
+        if (rc) return rc;
+    }
     return LC_OK;
 }
 
 int build_graph(lc_ctx *c) {
     release_graph(c);
-    const Layout &L = c->lay;
-    int N = c->N, P = L.Pl[0];
-    double *W0 = c->at<double>(L.W0), *Wa = c->at<double>(L.Wa), *Wb = c->at<double>(L.Wb);
-    double *ACC = c->at<double>(L.ACC), *psi = c->psi(0);
-    double dt = c->dt;
-    StageCoef k1{1.0, 0.0, B10 * dt, 0.0, 0.0, 0};
-    StageCoef k2{A20, A21, B21 * dt, 0.0, 0.0, 0};
-    StageCoef k3{A30, A32, B32 * dt, A52, 0.0, 1};
-    StageCoef k4{A40, A43, B43 * dt, A53, B53 * dt, 2};
-    StageCoef k5{0.0, A54, B54 * dt, 0.0, 0.0, 3};
-    struct {
-        const double *in;
-        double *out;
-        StageCoef k;
-    } stages[5] = {{W0, Wa, k1}, {Wa, Wb, k2}, {Wb, Wa, k3}, {Wa, Wb, k4}, {Wb, W0, k5}};
-
+    StagePlan st[5];
+    stage_plan(c, st);
     cudaStream_t s;
     LC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
@@ -265,12 +474,7 @@ int build_graph(lc_ctx *c) {
         return cuda_fail(e, "cudaStreamBeginCapture");
     }
     int rc = LC_OK;
-    for (int k = 0; k < 5 && rc == LC_OK; ++k) {
-        cudaError_t le = launch_rhs_stage(s, psi, stages[k].in, W0, ACC, stages[k].out, N, P, c->Re, c->advect,
-                                          stages[k].k);
-        if (le != cudaSuccess) rc = cuda_fail(le, "launch_rhs_stage");
-        if (rc == LC_OK) rc = capture_solve(c, s, stages[k].out);
-    }
+    for (int k = 0; k < 5 && rc == LC_OK; ++k) rc = capture_stage(c, s, st[k]);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(s, &g);
     cudaStreamDestroy(s);
@@ -280,7 +484,8 @@ int build_graph(lc_ctx *c) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     c->graph = g;
-    c->kernels_per_step = 5 * 3;  // per stage: L + combination, Poisson right-hand side, Thom
+    // per stage: L + combination, Poisson right-hand side, (mixed: first residual), Thom
+    c->kernels_per_step = 5 * (c->mixed() ? 4 : 3);
     LC_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
     c->graph_dirty = false;
     return LC_OK;
@@ -289,6 +494,7 @@ int build_graph(lc_ctx *c) {
 int ensure_init(lc_ctx *c) {
     if (c->initialized) return LC_OK;
     LC_CUDA(cudaGetDevice(&c->device));
+    LC_CUDA(init_mg_kernel_attributes());
     if (!c->ws) {
         void *p = nullptr;
         LC_CUDA(cudaMalloc(&p, c->lay.total));
@@ -300,9 +506,8 @@ int ensure_init(lc_ctx *c) {
     if (!c->cap2) LC_CUDA(cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking));
     cudaStream_t s = c->stream();
     LC_CUDA(cudaMemsetAsync(c->ws, 0, c->lay.total, s));
-    const Layout &L = c->lay;
-    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), c->N, L.Pl[0],
-                        c->U, c->profile));
+    int rc = enqueue_thom(c, s);
+    if (rc) return rc;
     c->initialized = true;
     return LC_OK;
 }
@@ -426,7 +631,6 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "precision") {
         if (c->initialized) return fail(LC_ERR_ARG, "precision must be set before first use");
         if (!integral || (iv != LC_PREC_FP64 && iv != LC_PREC_MIXED)) return fail(LC_ERR_ARG, "precision must be 0 or 1");
-        if (iv == LC_PREC_MIXED) return fail(LC_ERR_ARG, "mixed precision is not available in this build");
         c->precision = iv;
         make_layout(c->N, c->precision, c->lay);
     } else if (k == "nu1" || k == "nu2") {
@@ -450,13 +654,22 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
             c->profile = iv;
         }
         if (c->initialized) {
-            const Layout &L = c->lay;
-            LC_CUDA(launch_thom(c->stream(), c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa),
-                                c->at<double>(L.Wb), c->N, L.Pl[0], c->U, c->profile));
+            int rc = enqueue_thom(c, c->stream());
+            if (rc) return rc;
         }
     } else if (k == "advect") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "advect must be 0 or 1");
         c->advect = iv;
+    } else if (k == "blocked" || k == "fine_phases") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, k + " must be 0 or 1");
+        (k == "blocked" ? c->blocked : c->fine_phases) = iv;
+    } else if (k == "coarse_max") {
+        if (!integral || iv < 2 || iv > 256) return fail(LC_ERR_ARG, "coarse_max must be 2..256");
+        c->coarse_max = iv;
+    } else if (k == "graph") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "graph must be 0 or 1");
+        c->use_graph = iv;
+        return LC_OK;
     } else if (k == "monitor") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "monitor must be 0 or 1");
         c->monitor = iv;
@@ -473,7 +686,7 @@ int lc_step(lc_ctx *c, int nsteps) {
     if (nsteps < 0) return fail(LC_ERR_ARG, "nsteps must be >= 0");
     int rc = ensure_init(c);
     if (rc) return rc;
-    if (c->graph_dirty) {
+    if (c->use_graph && c->graph_dirty) {
         rc = build_graph(c);
         if (rc) return rc;
     }
@@ -486,7 +699,12 @@ int lc_step(lc_ctx *c, int nsteps) {
             LC_CUDA(cudaMemcpyAsync(c->at<double>(L.snap_psi), c->psi(0), fb, cudaMemcpyDeviceToDevice, s));
             LC_CUDA(cudaMemcpyAsync(c->at<double>(L.snap_w), c->at<double>(L.W0), fb, cudaMemcpyDeviceToDevice, s));
         }
-        LC_CUDA(cudaGraphLaunch(c->exec, s));
+        if (c->use_graph) {
+            LC_CUDA(cudaGraphLaunch(c->exec, s));
+        } else {
+            rc = eager_step(c);
+            if (rc) return rc;
+        }
         if (last && c->monitor) {
             LC_CUDA(launch_monitor(s, c->at<double>(L.snap_psi), c->psi(0), c->at<double>(L.snap_w),
                                    c->at<double>(L.W0), c->N, L.Pl[0], c->at<double>(L.mpart), c->ds(), c->dt));
@@ -548,8 +766,12 @@ int lc_set_state(lc_ctx *c, const double *psi, const double *omega) {
     LC_CUDA(cudaMemcpy2DAsync(c->psi(0), dp, psi, hp, hp, c->N + 1, cudaMemcpyHostToDevice, s));
     LC_CUDA(launch_zero_walls(s, c->psi(0), c->N, L.Pl[0]));
     LC_CUDA(cudaMemcpy2DAsync(c->at<double>(L.W0), dp, omega, hp, hp, c->N + 1, cudaMemcpyHostToDevice, s));
-    LC_CUDA(launch_thom(s, c->psi(0), c->at<double>(L.W0), c->at<double>(L.Wa), c->at<double>(L.Wb), c->N, L.Pl[0],
-                        c->U, c->profile));
+    if (c->mixed()) {
+        LC_CUDA(launch_to32(s, c->psi(0), L.Pl[0], c->at<float>(L.psi32), L.Pl[0], c->N));
+        LC_CUDA(launch_to32(s, c->at<double>(L.W0), L.Pl[0], c->at<float>(L.W0s), L.Pl[0], c->N));
+    }
+    rc = enqueue_thom(c, s);
+    if (rc) return rc;
     LC_CUDA(cudaStreamSynchronize(s));  // the host arrays may be released on return
     return LC_OK;
 }
@@ -592,38 +814,61 @@ int lc_launch_stats(lc_ctx *c, double out[2]) {
         if (rc == LC_OK) rc = build_graph(c);
         if (rc) return rc;
     }
-    out[0] = c->kernels_per_step + (c->monitor ? 1 : 0);
+    out[0] = c->kernels_per_step + (c->monitor ? 1 : 0);  // the same kernels in graph and eager mode
     out[1] = c->kernels_per_cycle;
     return LC_OK;
 }
 
 int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
     LC_CHECK_CTX(c);
-    if (!out || reps < 1 || kernel < 0 || kernel > 2) return fail(LC_ERR_ARG, "bad kernel id, reps or output");
+    int nk = c->mixed() ? 4 : 3;
+    if (!out || reps < 1 || kernel < 0 || kernel >= nk) return fail(LC_ERR_ARG, "bad kernel id, reps or output");
     int rc = ensure_init(c);
     if (rc) return rc;
     cudaStream_t s = c->stream();
     const Layout &L = c->lay;
     int N = c->N, P = L.Pl[0];
-    double n_int = (double)(N - 1) * (N - 1);
+    double n_int = (double)(N - 1) * (N - 1), n_c = (double)(N / 2 - 1) * (N / 2 - 1);
+    int ncol = c->op == LC_OP_COMPACT ? 4 : 2;
+    double sw_flops = c->op == LC_OP_COMPACT ? 10.0 : 5.0;  // per node per sweep: 6 adds + 2 FMAs (5-point: 3 + 1)
+    double res_flops = sw_flops + 1.0;
+    StageCoef k2{A20, A21, B21 * c->dt, 0.0, 0.0, 0};
+    auto launch = [&](int r) -> cudaError_t {
+        if (!c->mixed()) {
+            switch (kernel) {
+                case 0:
+                    return launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), N, P, r % ncol, c->beta);
+                case 1:
+                    return launch_rhs_stage(s, c->psi(0), c->at<double>(L.Wa), c->at<double>(L.W0),
+                                            c->at<double>(L.ACC), c->at<double>(L.Wb), N, P, c->Re, c->advect, k2);
+                default:
+                    return launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), N, P, c->g(1), c->psi(1),
+                                                            L.Pl[1]);
+            }
+        }
+        switch (kernel) {
+            case 0:
+                return launch_down<float>(s, c->op, nullptr, 1, c->g32(0), c->eB(0), N, P, c->g32(1), L.Pl[1], c->nu1,
+                                          (float)c->beta);
+            case 1:
+                return launch_rhs_stage_mixed(s, c->at<float>(L.psi32), P, c->at<float>(L.Was), c->at<double>(L.Wa),
+                                              c->at<double>(L.W0), c->at<double>(L.ACC), c->at<double>(L.Wb),
+                                              c->at<float>(L.Wbs), N, P, P, c->Re, c->advect, k2);
+            case 2:
+                return launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
+                                              c->at<double>(L.rpart));
+            default: {
+                Correct64 cor{c->psi(0), P, c->at<float>(L.psi32), P};
+                return launch_up<float>(s, c->op, c->eB(0), c->g32(0), c->eA(1), L.Pl[1], c->eA(0), N, P, c->nu2,
+                                        (float)c->beta, nullptr, cor);
+            }
+        }
+    };
+    if (c->mixed() && (kernel == 0 || kernel == 3) && coarse_level(c) == 0)
+        return fail(LC_ERR_ARG, "grid too small for the tile kernels");
     cudaEvent_t e0, e1;
     LC_CUDA(cudaEventCreate(&e0));
     LC_CUDA(cudaEventCreate(&e1));
-    int ncol = c->op == LC_OP_COMPACT ? 4 : 2;
-    auto launch = [&](int r) -> cudaError_t {
-        switch (kernel) {
-            case 0:
-                return launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), N, P, r % ncol, c->beta);
-            case 1: {
-                StageCoef k2{A20, A21, B21 * c->dt, 0.0, 0.0, 0};
-                return launch_rhs_stage(s, c->psi(0), c->at<double>(L.Wa), c->at<double>(L.W0), c->at<double>(L.ACC),
-                                        c->at<double>(L.Wb), N, P, c->Re, c->advect, k2);
-            }
-            default:
-                return launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), N, P, c->g(1), c->psi(1),
-                                                        L.Pl[1]);
-        }
-    };
     LC_CUDA(launch(0));  // warm the instruction cache
     LC_CUDA(cudaEventRecord(e0, s));
     for (int r = 0; r < reps; ++r) LC_CUDA(launch(r));
@@ -634,25 +879,43 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     out[0] = ms / reps;
-    switch (kernel) {
-        case 0: {  // read psi once, read g and write psi at the colour's nodes
-            double nc = n_int / ncol;
-            out[1] = 8.0 * n_int + 16.0 * nc;
-            // compact: 6 adds + 2 FMAs; 5-point: 3 adds + 1 FMA; relaxation adds a subtract and an FMA
-            double per = (c->op == LC_OP_COMPACT ? 10.0 : 5.0) + (c->beta != 1.0 ? 3.0 : 0.0);
-            out[2] = per * nc;
-            out[3] = 0.0;
-            break;
+    out[2] = out[3] = 0.0;
+    if (!c->mixed()) {
+        switch (kernel) {
+            case 0: {  // read psi once, read g and write psi at the colour's nodes
+                double nc = n_int / ncol;
+                out[1] = 8.0 * n_int + 16.0 * nc;
+                out[2] = (sw_flops + (c->beta != 1.0 ? 3.0 : 0.0)) * nc;
+                break;
+            }
+            case 1:  // stage 2: read omega^(1), psi, omega^n; write omega^(2)
+                out[1] = 32.0 * n_int;
+                out[2] = (c->advect ? 27.0 : 13.0) * n_int;
+                break;
+            default:  // read psi, g; write the coarse g and zero the coarse psi
+                out[1] = 16.0 * n_int + 16.0 * n_c;
+                out[2] = res_flops * n_int + 8.0 * n_c;
         }
-        case 1:  // stage 2: read omega^(1), psi, omega^n; write omega^(2)
-            out[1] = 32.0 * n_int;
-            out[2] = (c->advect ? 27.0 : 13.0) * n_int;
-            out[3] = 0.0;
-            break;
-        default:  // read psi, g; write the coarse g and zero the coarse psi
-            out[1] = 16.0 * n_int + 16.0 * (N / 2 - 1) * (N / 2 - 1);
-            out[2] = (c->op == LC_OP_COMPACT ? 11.0 : 6.0) * n_int + 8.0 * (N / 2 - 1) * (N / 2 - 1);
-            out[3] = 0.0;
+    } else {
+        switch (kernel) {
+            case 0:  // read r32; write e32 and the coarse g32; nu1 sweeps + residual + restriction in FP32
+                out[1] = 8.0 * n_int + 4.0 * n_c;
+                out[3] = (c->nu1 * sw_flops + res_flops) * n_int + 8.0 * n_c;
+                break;
+            case 1:  // read omega32 (stencil), psi32, omega64, W0; write omega64 and its shadow
+                out[1] = 36.0 * n_int;
+                out[2] = 5.0 * n_int;
+                out[3] = (c->advect ? 22.0 : 8.0) * n_int;
+                break;
+            case 2:  // read psi64, g64; write r32
+                out[1] = 20.0 * n_int;
+                out[2] = (res_flops + 1.0) * n_int;
+                break;
+            default:  // read e32, r32, coarse e, psi64; write psi64 and psi32
+                out[1] = 28.0 * n_int + 4.0 * n_c;
+                out[2] = 1.0 * n_int;
+                out[3] = (c->nu2 * sw_flops + 3.0) * n_int;
+        }
     }
     return LC_OK;
 }

@@ -35,7 +35,7 @@ struct DevState {
     int cycles;       // V-cycles done in the solve in progress
     int status;       // kStatus* bits, sticky until read by the host
     int last_cycles;  // cycles of the last finished solve
-    int pad0;
+    int more;         // eager mode: 1 if the V-cycle loop goes on
     double last_rel;  // relative residual at the end of the last solve
     unsigned long long nsolves;
     double mon[3];    // max|d omega|/dt, RES_psi, RES_omega
@@ -71,6 +71,7 @@ int assemble_blocks(int N);
 int monitor_blocks(int N);
 
 cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, double *g, int N, int P, double *gpart);
+// h != 0: sets the graph while-node's condition; h == 0 (eager mode): writes ds->more.
 cudaError_t launch_finish_norm(cudaStream_t s, const double *rpart, int nr, const double *gpart, int ng, DevState *ds,
                                cudaGraphConditionalHandle h, double tol, int max_cycles);
 cudaError_t launch_thom(cudaStream_t s, const double *psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
@@ -80,6 +81,44 @@ cudaError_t launch_rhs_stage(cudaStream_t s, const double *psi, const double *in
 cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi1, const double *w0, const double *w1,
                            int N, int P, double *part, DevState *ds, double dt);
 cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P);
+
+// FP64 correction target of the mixed-precision fine level (psi64 == nullptr: none).
+struct Correct64 {
+    double *psi64;
+    int P64;
+    float *psi32;
+    int P32;
+};
+
+// ---- shared-memory multigrid kernels (lc_mg.cu)
+bool use_big_tiles(int N);
+int tiles_of(int N);
+size_t tile_smem_bytes(int N, int op, int nu, int elem);
+size_t coarse_smem_bytes(int N0, int nl, int elem);
+template <typename T>
+cudaError_t launch_down(cudaStream_t s, int op, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
+                        T *gc, int Pc, int nu, T beta);
+template <typename T>
+cudaError_t launch_up(cudaStream_t s, int op, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
+                      int P, int nu, T beta, double *partials, Correct64 cor);
+template <typename T>
+cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T *psi_warm, T *psi_out, int Po, int N0,
+                          int nl, int nu1, int nu2, int nuc, T beta, double *partial);
+
+constexpr size_t kMaxSmem = 227 * 1024;
+cudaError_t init_mg_kernel_attributes();
+
+// ---- mixed-precision kernels (lc_mixed.cu)
+cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
+                                   float *r32, int P32, double *partials);
+cudaError_t launch_correct64(cudaStream_t s, const float *e32, int Pe, double *psi64, int P64, float *psi32, int P32,
+                             int N);
+cudaError_t launch_rhs_stage_mixed(cudaStream_t s, const float *psi32, int Ps, const float *in32, const double *in64,
+                                   const double *W0, double *acc, double *out64, float *out32, int N, int P64, int P32,
+                                   double Re, int advect, StageCoef c);
+cudaError_t launch_thom_mixed(cudaStream_t s, const double *psi64, double *const w64[3], float *const w32[3], int N,
+                              int P64, int P32, double U, int profile);
+cudaError_t launch_to32(cudaStream_t s, const double *src, int P64, float *dst, int P32, int N);
 
 // Sets the calling thread's lc_last_error() message.
 void set_last_error(const char *msg);

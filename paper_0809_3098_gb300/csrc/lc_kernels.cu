@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 // and sets the while-node's condition.  Stopping rule: ||rho|| <= tol ||g||,
 // checked after every cycle; a non-finite norm or max_cycles ends the loop
 // with a status bit.
+template <bool kGraph>
 __global__ void k_finish_norm(const double *__restrict__ rpart, int nr, const double *__restrict__ gpart, int ng,
                               DevState *ds, cudaGraphConditionalHandle h, double tol, int max_cycles) {
     __shared__ double sh[32];
@@ -244,7 +245,10 @@ __global__ void k_finish_norm(const double *__restrict__ rpart, int nr, const do
         ds->log[ds->nsolves % kLogN] = cyc;
         ds->nsolves += 1;
     }
-    cudaGraphSetConditional(h, more);
+    if (kGraph)
+        cudaGraphSetConditional(h, more);
+    else
+        ds->more = (int)more;
 }
 
 // Thom's wall vorticity, Eq. (25): -2 psi_adjacent / h^2 on every wall, minus
@@ -447,7 +451,10 @@ cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, dou
 
 cudaError_t launch_finish_norm(cudaStream_t s, const double *rpart, int nr, const double *gpart, int ng, DevState *ds,
                                cudaGraphConditionalHandle h, double tol, int max_cycles) {
-    k_finish_norm<<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
+    if (h)
+        k_finish_norm<true><<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
+    else
+        k_finish_norm<false><<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
     return cudaGetLastError();
 }
 

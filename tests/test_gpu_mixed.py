@@ -1,0 +1,100 @@
+"""Mixed-precision path: FP32 V-cycles and FP32 L(omega) stencils inside FP64
+residual, refinement, Thom and stage accumulation.
+
+Every Poisson solve still stops on the FP64 relative residual tol, so the
+pressure-free part of the error is FP64's; what FP32 adds is rounding in
+L(omega).  Bar: 1e-6 relative (max-norm) in psi and omega against the FP64
+oracle / FP64 GPU path on the same workload.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0809_3098_gb300 import lc
+from paper_0809_3098_gb300.workloads import dt_rule, smooth_random_state
+
+pytestmark = pytest.mark.gpu
+MIXED = lc.LC_PREC_MIXED
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("N", [16, 24, 64, 128])
+@pytest.mark.parametrize("op", [lc.LC_OP_5PT, lc.LC_OP_COMPACT])
+def test_mixed_matches_oracle(N, op):
+    Re, steps = 1000.0, 5
+    dt = dt_rule(N, Re)
+    g = lc.Cavity(N, Re, dt, 1e-10, op=op, precision=MIXED)
+    r = oracle.Cavity(N, Re, dt, 1e-10, op=op)
+    g.step(steps)
+    r.step(steps)
+    assert rel(g.psi(), r.psi()) < 1e-6 and rel(g.omega(), r.omega()) < 1e-6
+    assert g.residual() <= 1e-10
+    gl, rl = g.cycle_log(), r.cycle_log()
+    assert len(gl) == 5 * steps and np.abs(gl - rl).max() <= 2
+
+
+@pytest.mark.parametrize("coarse_max", [2, 16, 64, 256])
+def test_mixed_coarse_split_variants_agree(coarse_max):
+    N, Re = 96, 2000.0
+    a = lc.Cavity(N, Re, precision=MIXED, coarse_max=coarse_max)
+    b = lc.Cavity(N, Re)
+    a.step(4)
+    b.step(4)
+    assert rel(a.psi(), b.psi()) < 1e-6 and rel(a.omega(), b.omega()) < 1e-6
+
+
+def test_mixed_from_random_state():
+    N, Re = 128, 5000.0
+    psi, omega = smooth_random_state(N, seed=3)
+    a = lc.Cavity(N, Re, precision=MIXED)
+    b = lc.Cavity(N, Re)
+    a.set_state(psi, omega)
+    b.set_state(psi, omega)
+    assert np.array_equal(a.omega(), b.omega())
+    a.step(3)
+    b.step(3)
+    assert rel(a.psi(), b.psi()) < 1e-6 and rel(a.omega(), b.omega()) < 1e-6
+
+
+def test_mixed_graph_and_eager_identical():
+    N = 256
+    a = lc.Cavity(N, 3000.0, precision=MIXED)
+    b = lc.Cavity(N, 3000.0, precision=MIXED, graph=0)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
+    assert np.array_equal(a.cycle_log(), b.cycle_log())
+
+
+def test_mixed_1024_against_fp64_gpu():
+    """1024^2, Re 10^4, 20 steps: mixed against the FP64 GPU path (itself held
+    to the oracle at 1e-10)."""
+    N, Re = 1024, 10000.0
+    a = lc.Cavity(N, Re, precision=MIXED)
+    b = lc.Cavity(N, Re)
+    a.step(20)
+    b.step(20)
+    ep, ew = rel(a.psi(), b.psi()), rel(a.omega(), b.omega())
+    assert ep < 1e-6 and ew < 1e-6, (ep, ew)
+    ca, cb = a.cycle_log(), b.cycle_log()
+    assert abs(ca.mean() - cb.mean()) < 1.0
+
+
+def test_mixed_lid_reversal_equivariance_bitwise():
+    N = 512
+    a = lc.Cavity(N, 10000.0, precision=MIXED)
+    b = lc.Cavity(N, 10000.0, precision=MIXED, U=-1.0)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(b.psi(), -a.psi()[:, ::-1]) and np.array_equal(b.omega(), -a.omega()[:, ::-1])
+
+
+def test_mixed_errors_reported():
+    g = lc.Cavity(64, 1000.0, precision=MIXED, max_cycles=1, tol=1e-14)
+    g.step(1)
+    with pytest.raises(lc.LCError) as e:
+        g.synchronize()
+    assert e.value.code == lc.LC_ERR_NOCONV
