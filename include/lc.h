@@ -117,6 +117,17 @@ const char *lc_last_error(void);
  *   "advect"      1 (default), 0 drops the transport terms of Eq. (8)
  *   "monitor"     1 computes lc_monitor's values over the last step of each
  *                 lc_step call (default 0)
+ *   "blocked"     1 (default): levels above the coarse ones run as shared-
+ *                 memory tile kernels (all colour phases of a level's smoothing
+ *                 in one launch, halos recomputed); 0: one launch per colour
+ *                 phase on every level.  FP64 only; results are identical.
+ *   "fine_phases" 1 (default): with "blocked", the finest FP64 level still
+ *                 uses one launch per colour phase (no recomputed halo).
+ *   "coarse_max"  levels with at most this many intervals run as one V-cycle
+ *                 in a single thread block (default -1: 32 for FP64, 64 for
+ *                 mixed precision), 2..256.
+ *   "tile_shape"  -1 (default) picks each level's tile shape; 0..3 forces
+ *                 128x64, 64x64, 32x32 or 16x16 owned nodes per tile.
  *   "graph"       1 (default) replays each step as one CUDA graph whose
  *                 V-cycle loops are device-side while-nodes; 0 launches the
  *                 same kernels one by one and drives the V-cycle loop from the

@@ -129,7 +129,7 @@ bool make_layout(int N, int precision, Layout &L) {
     L.snap_psi = take(n0 * sizeof(double));
     L.snap_w = take(n0 * sizeof(double));
     L.nrpart_grid = residual_norm_blocks(N);
-    L.nrpart = L.nrpart_grid > tiles_of(N) ? L.nrpart_grid : tiles_of(N);
+    L.nrpart = L.nrpart_grid > tiles_of(N, 3) ? L.nrpart_grid : tiles_of(N, 3);  // 16x16 tiles: the most partials
     L.ngpart = assemble_blocks(N);
     L.nmpart = monitor_blocks(N);
     L.rpart = take(L.nrpart * sizeof(double));
@@ -152,6 +152,7 @@ struct lc_ctx {
     int use_graph = 1;
     double beta = 1.0, U = 1.0;
     int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
+    int tile_force = -1;                                // >= 0: one tile shape on every level
 
     Layout lay;
     char *ws = nullptr;
@@ -216,6 +217,11 @@ int coarse_level(const lc_ctx *c) {
     return L.nlev - 1;
 }
 
+int tile_shape(const lc_ctx *c, int l) {
+    int nu = c->nu1 > c->nu2 ? c->nu1 : c->nu2;
+    return tile_shape_for(c->lay.Nl[l], c->op, nu, c->mixed() ? 4 : 8, c->tile_force);
+}
+
 // Whether the shared-memory tile kernels can run every level above the
 // coarse level with the current smoothing counts.
 bool blocked_ok(const lc_ctx *c) {
@@ -223,7 +229,7 @@ bool blocked_ok(const lc_ctx *c) {
     int lc = coarse_level(c);
     int nu = c->nu1 > c->nu2 ? c->nu1 : c->nu2;
     for (int l = 0; l < lc; ++l)
-        if (tile_smem_bytes(c->lay.Nl[l], c->op, nu, c->mixed() ? 4 : 8) > kMaxSmem - 1024) return false;
+        if (tile_smem_bytes(tile_shape(c, l), c->op, nu, c->mixed() ? 4 : 8) > kMaxSmem - 1024) return false;
     return true;
 }
 
@@ -251,9 +257,17 @@ int enqueue_vcycle_phases(lc_ctx *c, cudaStream_t s) {
     return LC_OK;
 }
 
-// Enqueues one FP64 V-cycle on stream s.  Sets *norm_done when the cycle's
-// last kernel already wrote the fine-level residual partials.
-int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done) {
+FinishArgs finish_args(const lc_ctx *c, int nr, cudaGraphConditionalHandle h) {
+    const Layout &L = c->lay;
+    return FinishArgs{1, nr, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol, c->max_cycles};
+}
+
+const FinishArgs kNoFinish{0, 0, nullptr, 0, nullptr, 0, 0.0, 0};
+
+// Enqueues one FP64 V-cycle on stream s.  When the cycle's last kernel writes
+// the fine-level residual partials it also takes the end-of-cycle decision
+// (*norm_done = true); otherwise the caller adds the residual-norm kernel.
+int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditionalHandle h) {
     *norm_done = false;
     if (!blocked_ok(c)) return enqueue_vcycle_phases(c, s);
     const Layout &L = c->lay;
@@ -270,13 +284,14 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done) {
             LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], c->g(1),
                                                      c->psi(1), L.Pl[1]));
         } else {
-            LC_CUDA(launch_down<double>(s, c->op, c->psi(l), l > 0, c->g(l), c->psiB(l), L.Nl[l], L.Pl[l], c->g(l + 1),
-                                        L.Pl[l + 1], c->nu1, c->beta));
+            LC_CUDA(launch_down<double>(s, tile_shape(c, l), c->op, c->psi(l), l > 0, c->g(l), c->psiB(l), L.Nl[l],
+                                        L.Pl[l], c->g(l + 1), L.Pl[l + 1], c->nu1, c->beta));
         }
         ++k;
     }
     LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], lc == 0 ? c->psi(0) : nullptr, c->psi(lc), L.Pl[lc],
-                                  L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, lc == 0 ? rpart : nullptr));
+                                  L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, lc == 0 ? rpart : nullptr,
+                                  lc == 0 ? finish_args(c, 1, h) : kNoFinish));
     ++k;
     Correct64 none{nullptr, 0, nullptr, 0};
     for (int l = lc - 1; l >= 0; --l) {
@@ -286,8 +301,9 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done) {
                 for (int col = 0; col < nc; ++col, ++k)
                     LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta));
         } else {
-            LC_CUDA(launch_up<double>(s, c->op, c->psiB(l), c->g(l), c->psi(l + 1), L.Pl[l + 1], c->psi(l), L.Nl[l],
-                                      L.Pl[l], c->nu2, c->beta, l == 0 ? rpart : nullptr, none));
+            LC_CUDA(launch_up<double>(s, tile_shape(c, l), c->op, c->psiB(l), c->g(l), c->psi(l + 1), L.Pl[l + 1],
+                                      c->psi(l), L.Nl[l], L.Pl[l], c->nu2, c->beta, l == 0 ? rpart : nullptr, none,
+                                      l == 0 ? finish_args(c, 0, h) : kNoFinish));
         }
         ++k;
     }
@@ -300,16 +316,16 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done) {
 // correction e of L_h e = r (r = the FP64 residual rounded to FP32, starting
 // from e = 0), psi64 += e on the fine level, then the new FP64 residual with
 // its norm partials (which also becomes the next step's r).
-int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s) {
+int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const Layout &L = c->lay;
     int lc = coarse_level(c);
     float beta = (float)c->beta;
     int k = 0;
     for (int l = 0; l < lc; ++l, ++k)
-        LC_CUDA(launch_down<float>(s, c->op, nullptr, 1, c->g32(l), c->eB(l), L.Nl[l], L.Pl[l], c->g32(l + 1),
-                                   L.Pl[l + 1], c->nu1, beta));
+        LC_CUDA(launch_down<float>(s, tile_shape(c, l), c->op, nullptr, 1, c->g32(l), c->eB(l), L.Nl[l], L.Pl[l],
+                                   c->g32(l + 1), L.Pl[l + 1], c->nu1, beta));
     LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc], L.nlev - lc,
-                                 c->nu1, c->nu2, c->nuc, beta, nullptr));
+                                 c->nu1, c->nu2, c->nuc, beta, nullptr, kNoFinish));
     ++k;
     float *psi32 = c->at<float>(L.psi32);
     if (lc == 0) {
@@ -319,40 +335,29 @@ int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s) {
     for (int l = lc - 1; l >= 0; --l, ++k) {
         Correct64 cor{nullptr, 0, nullptr, 0};
         if (l == 0) cor = Correct64{c->psi(0), L.Pl[0], psi32, L.Pl[0]};
-        LC_CUDA(launch_up<float>(s, c->op, c->eB(l), c->g32(l), c->eA(l + 1), L.Pl[l + 1], c->eA(l), L.Nl[l], L.Pl[l],
-                                 c->nu2, beta, nullptr, cor));
+        LC_CUDA(launch_up<float>(s, tile_shape(c, l), c->op, c->eB(l), c->g32(l), c->eA(l + 1), L.Pl[l + 1], c->eA(l),
+                                 L.Nl[l], L.Pl[l], c->nu2, beta, nullptr, cor, kNoFinish));
     }
     LC_CUDA(launch_residual64_to32(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<float>(L.r32), L.Pl[0],
-                                   c->at<double>(L.rpart)));
+                                   c->at<double>(L.rpart), finish_args(c, L.nrpart_grid, h)));
     c->kernels_per_cycle = k + 1;
     return LC_OK;
 }
 
-// Body of one iteration of a Poisson loop: a cycle, the residual norm and the
-// finisher (h != 0: sets the graph while-node's condition; h == 0: eager).
+// Body of one iteration of a Poisson loop: a cycle whose last kernel also
+// computes the residual norm and takes the end-of-cycle decision (h != 0: the
+// graph while-node's condition; h == 0: eager).
 int enqueue_cycle_body(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const Layout &L = c->lay;
-    double *rpart = c->at<double>(L.rpart);
-    int nparts;
-    if (c->mixed()) {
-        int rc = enqueue_vcycle_mixed(c, s);
-        if (rc) return rc;
-        nparts = L.nrpart_grid;
-    } else {
-        bool norm_done = false;
-        int rc = enqueue_vcycle(c, s, &norm_done);
-        if (rc) return rc;
-        if (!norm_done) {
-            LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], rpart));
-            c->kernels_per_cycle += 1;
-            nparts = L.nrpart_grid;
-        } else {
-            nparts = coarse_level(c) == 0 ? 1 : tiles_of(c->N);
-        }
+    if (c->mixed()) return enqueue_vcycle_mixed(c, s, h);
+    bool norm_done = false;
+    int rc = enqueue_vcycle(c, s, &norm_done, h);
+    if (rc) return rc;
+    if (!norm_done) {
+        LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<double>(L.rpart),
+                                             finish_args(c, L.nrpart_grid, h)));
+        c->kernels_per_cycle += 1;
     }
-    LC_CUDA(launch_finish_norm(s, rpart, nparts, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol,
-                               c->max_cycles));
-    c->kernels_per_cycle += 1;
     return LC_OK;
 }
 
@@ -399,7 +404,7 @@ int enqueue_stage_head(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
                                        c->at<double>(L.ACC), st.out64, st.out32, N, P, P, c->Re, c->advect, st.k));
         LC_CUDA(launch_assemble_rhs(s, c->op, st.out64, c->g(0), N, P, c->at<double>(L.gpart)));
         LC_CUDA(launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
-                                       c->at<double>(L.rpart)));
+                                       c->at<double>(L.rpart), kNoFinish));
     } else {
         LC_CUDA(launch_rhs_stage(s, c->psi(0), st.in64, c->at<double>(L.W0), c->at<double>(L.ACC), st.out64, N, P,
                                  c->Re, c->advect, st.k));
@@ -663,6 +668,9 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "blocked" || k == "fine_phases") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, k + " must be 0 or 1");
         (k == "blocked" ? c->blocked : c->fine_phases) = iv;
+    } else if (k == "tile_shape") {
+        if (!integral || iv < -1 || iv > 3) return fail(LC_ERR_ARG, "tile_shape must be -1 (auto) or 0..3");
+        c->tile_force = iv;
     } else if (k == "coarse_max") {
         if (!integral || iv < 2 || iv > 256) return fail(LC_ERR_ARG, "coarse_max must be 2..256");
         c->coarse_max = iv;
@@ -848,19 +856,19 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
         }
         switch (kernel) {
             case 0:
-                return launch_down<float>(s, c->op, nullptr, 1, c->g32(0), c->eB(0), N, P, c->g32(1), L.Pl[1], c->nu1,
-                                          (float)c->beta);
+                return launch_down<float>(s, tile_shape(c, 0), c->op, nullptr, 1, c->g32(0), c->eB(0), N, P, c->g32(1),
+                                          L.Pl[1], c->nu1, (float)c->beta);
             case 1:
                 return launch_rhs_stage_mixed(s, c->at<float>(L.psi32), P, c->at<float>(L.Was), c->at<double>(L.Wa),
                                               c->at<double>(L.W0), c->at<double>(L.ACC), c->at<double>(L.Wb),
                                               c->at<float>(L.Wbs), N, P, P, c->Re, c->advect, k2);
             case 2:
                 return launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
-                                              c->at<double>(L.rpart));
+                                              c->at<double>(L.rpart), kNoFinish);
             default: {
                 Correct64 cor{c->psi(0), P, c->at<float>(L.psi32), P};
-                return launch_up<float>(s, c->op, c->eB(0), c->g32(0), c->eA(1), L.Pl[1], c->eA(0), N, P, c->nu2,
-                                        (float)c->beta, nullptr, cor);
+                return launch_up<float>(s, tile_shape(c, 0), c->op, c->eB(0), c->g32(0), c->eA(1), L.Pl[1], c->eA(0), N,
+                                        P, c->nu2, (float)c->beta, nullptr, cor, kNoFinish);
             }
         }
     };

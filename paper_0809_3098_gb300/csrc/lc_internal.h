@@ -39,7 +39,8 @@ struct DevState {
     double last_rel;  // relative residual at the end of the last solve
     unsigned long long nsolves;
     double mon[3];    // max|d omega|/dt, RES_psi, RES_omega
-    double pad1;
+    unsigned int arrive;  // blocks that have written their residual partial (fused finisher)
+    unsigned int pad1;
     int log[kLogN];   // cycles per solve, ring buffer indexed by nsolves
 };
 
@@ -53,6 +54,91 @@ struct StageCoef {
     int mode;
 };
 
+// Arguments of the end-of-cycle decision that the last block of a kernel
+// producing residual partials takes (enabled = 0: partials only).  The last
+// block sums the nr residual partials and the ng right-hand-side partials in
+// a fixed order, applies the stopping rule ||rho|| <= tol ||g|| (after every
+// cycle; NaN/Inf or max_cycles end the loop with a status bit) and either
+// sets the graph while-node's condition (h != 0) or writes ds->more (eager).
+struct FinishArgs {
+    int enabled;
+    int nr;
+    const double *gpart;
+    int ng;
+    DevState *ds;
+    cudaGraphConditionalHandle h;
+    double tol;
+    int max_cycles;
+};
+
+#ifdef __CUDACC__
+__device__ __forceinline__ double finish_block_sum(double v, double *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int t = threadIdx.y * blockDim.x + threadIdx.x;
+    int lane = t & 31, warp = t >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (warp == 0) {
+        r = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;  // valid in thread 0
+}
+
+// Called by every thread of every block after thread 0 of the block has
+// stored the block's residual partial; the last block of the grid to arrive
+// takes the decision described at FinishArgs.
+__device__ __forceinline__ void finish_if_last(const double *partials, FinishArgs fin) {
+    __shared__ unsigned int s_last;
+    __shared__ double s_red[32];
+    int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    unsigned int nb = gridDim.x * gridDim.y;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&fin.ds->arrive, 1u) == nb - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double sr = 0.0, sg = 0.0;
+    for (int k = tid; k < (int)nb; k += nt) sr += __ldcg(partials + k);  // one partial per block
+    for (int k = tid; k < fin.ng; k += nt) sg += __ldcg(fin.gpart + k);
+    sr = finish_block_sum(sr, s_red);
+    sg = finish_block_sum(sg, s_red);
+    if (tid != 0) return;
+    DevState *ds = fin.ds;
+    ds->arrive = 0;
+    int cyc = ds->cycles + 1;
+    double rn = sqrt(sr), gn = sqrt(sg);
+    bool finite = isfinite(rn) && isfinite(gn);
+    unsigned int more = 0;
+    if (!finite) {
+        ds->status |= kStatusNonFinite;
+    } else if (rn <= fin.tol * gn) {
+    } else if (cyc >= fin.max_cycles) {
+        ds->status |= kStatusNoConv;
+    } else {
+        more = 1;
+    }
+    if (more) {
+        ds->cycles = cyc;
+    } else {
+        ds->cycles = 0;
+        ds->last_cycles = cyc;
+        ds->last_rel = gn > 0.0 ? rn / gn : (rn > 0.0 ? INFINITY : 0.0);
+        ds->log[ds->nsolves % kLogN] = cyc;
+        ds->nsolves += 1;
+    }
+    if (fin.h)
+        cudaGraphSetConditional(fin.h, more);
+    else
+        ds->more = (int)more;
+}
+#endif
+
 // ---- launchers (lc_kernels.cu); each enqueues on `s` and returns the launch error
 template <typename T>
 cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int colour, T beta);
@@ -64,16 +150,14 @@ cudaError_t launch_prolong_correct(cudaStream_t s, T *psi, int Nf, int Pf, const
 template <typename T>
 cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta);
 template <typename T>
-cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials);
+cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials,
+                                 FinishArgs fin);
 
 int residual_norm_blocks(int N);
 int assemble_blocks(int N);
 int monitor_blocks(int N);
 
 cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, double *g, int N, int P, double *gpart);
-// h != 0: sets the graph while-node's condition; h == 0 (eager mode): writes ds->more.
-cudaError_t launch_finish_norm(cudaStream_t s, const double *rpart, int nr, const double *gpart, int ng, DevState *ds,
-                               cudaGraphConditionalHandle h, double tol, int max_cycles);
 cudaError_t launch_thom(cudaStream_t s, const double *psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
                         int profile);
 cudaError_t launch_rhs_stage(cudaStream_t s, const double *psi, const double *in, const double *W0, double *acc,
@@ -91,26 +175,29 @@ struct Correct64 {
 };
 
 // ---- shared-memory multigrid kernels (lc_mg.cu)
-bool use_big_tiles(int N);
-int tiles_of(int N);
-size_t tile_smem_bytes(int N, int op, int nu, int elem);
+// Tile shapes of the shared-memory kernels: 0 = 128x64, 1 = 64x64, 2 = 32x32,
+// 3 = 16x16 owned nodes.  tile_shape_for picks one per level (force >= 0
+// overrides).
+int tile_shape_for(int N, int op, int nu, int elem, int force);
+int tiles_of(int N, int shape);
+size_t tile_smem_bytes(int shape, int op, int nu, int elem);
 size_t coarse_smem_bytes(int N0, int nl, int elem);
 template <typename T>
-cudaError_t launch_down(cudaStream_t s, int op, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
-                        T *gc, int Pc, int nu, T beta);
+cudaError_t launch_down(cudaStream_t s, int shape, int op, const T *psi_in, int zero_init, const T *g, T *psi_out,
+                        int N, int P, T *gc, int Pc, int nu, T beta);
 template <typename T>
-cudaError_t launch_up(cudaStream_t s, int op, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
-                      int P, int nu, T beta, double *partials, Correct64 cor);
+cudaError_t launch_up(cudaStream_t s, int shape, int op, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out,
+                      int N, int P, int nu, T beta, double *partials, Correct64 cor, FinishArgs fin);
 template <typename T>
 cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T *psi_warm, T *psi_out, int Po, int N0,
-                          int nl, int nu1, int nu2, int nuc, T beta, double *partial);
+                          int nl, int nu1, int nu2, int nuc, T beta, double *partial, FinishArgs fin);
 
 constexpr size_t kMaxSmem = 227 * 1024;
 cudaError_t init_mg_kernel_attributes();
 
 // ---- mixed-precision kernels (lc_mixed.cu)
 cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
-                                   float *r32, int P32, double *partials);
+                                   float *r32, int P32, double *partials, FinishArgs fin);
 cudaError_t launch_correct64(cudaStream_t s, const float *e32, int Pe, double *psi64, int P64, float *psi32, int P32,
                              int N);
 cudaError_t launch_rhs_stage_mixed(cudaStream_t s, const float *psi32, int Ps, const float *in32, const double *in64,

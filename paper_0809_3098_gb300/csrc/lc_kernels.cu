@@ -67,7 +67,9 @@ __device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__rest
 // One colour phase of the SOR smoother, Eq. (15).  Compact: colour
 // (i mod 2) + 2 (j mod 2); 5-point: colour (i + j) mod 2.  Nodes of one colour
 // never neighbour each other, so the phase is a Jacobi update of that colour.
-template <typename T, int OP>
+// Each thread updates two nodes of the colour in one column, rows j and j+2,
+// which share the loads of row j+1; RELAX = false is the beta = 1 update.
+template <typename T, int OP, bool RELAX>
 __global__ void __launch_bounds__(kBX *kBY)
     k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
     int a = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,19 +77,47 @@ __global__ void __launch_bounds__(kBX *kBY)
     int i, j;
     if (OP == 1) {
         i = ((colour & 1) ? 1 : 2) + 2 * a;
-        j = ((colour >> 1) ? 1 : 2) + 2 * b;
+        j = ((colour >> 1) ? 1 : 2) + 4 * b;  // rows j and j + 2
     } else {
-        j = 1 + b;
+        // thread rows (1,3), (2,4), (5,7), (6,8), ...: j and j + 2 share a parity
+        j = 1 + 4 * (b >> 1) + (b & 1);
         i = (((colour + j) & 1) ? 1 : 2) + 2 * a;
     }
     if (i >= N || j >= N) return;
     size_t c = (size_t)j * P + i;
-    T v = gs_value<T, OP>(psi, g, c, P);
-    if (beta != T(1)) {
-        T old = psi[c];
-        v = fma(beta, v - old, old);
+    bool second = j + 2 < N;
+    size_t c2 = c + 2 * (size_t)P;
+    // shared row j + 1
+    T m_w = psi[c + P - 1], m_c = psi[c + P], m_e = psi[c + P + 1];
+    T v1, v2 = T(0);
+    {
+        T n4 = (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]);
+        if (OP == 1) {
+            T d4 = (m_e + m_w) + (psi[c - P + 1] + psi[c - P - 1]);
+            v1 = fma(T(0.2), n4, fma(T(0.05), d4, g[c]));
+        } else {
+            v1 = fma(T(0.25), n4, g[c]);
+        }
     }
-    psi[c] = v;
+    if (second) {
+        T n4 = (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c);
+        if (OP == 1) {
+            T d4 = (psi[c2 + P + 1] + psi[c2 + P - 1]) + (m_e + m_w);
+            v2 = fma(T(0.2), n4, fma(T(0.05), d4, g[c2]));
+        } else {
+            v2 = fma(T(0.25), n4, g[c2]);
+        }
+    }
+    if (RELAX) {
+        T o1 = psi[c];
+        v1 = fma(beta, v1 - o1, o1);
+        if (second) {
+            T o2 = psi[c2];
+            v2 = fma(beta, v2 - o2, o2);
+        }
+    }
+    psi[c] = v1;
+    if (second) psi[c2] = v2;
 }
 
 // Residual of the fine level, full-weighted onto the coarse level; also zeroes
@@ -170,7 +200,8 @@ __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, 
 // Per-block partial sums of rho^2 over interior nodes (FP64 accumulation).
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBX *kBY)
-    k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials) {
+    k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials,
+                    FinishArgs fin) {
     __shared__ double sh[32];
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -182,6 +213,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = v;
+    if (fin.enabled) finish_if_last(partials, fin);
 }
 
 // Scaled Poisson right-hand side at the fine level from omega:
@@ -208,47 +240,6 @@ __global__ void __launch_bounds__(kBX *kBY)
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) gpart[blockIdx.y * gridDim.x + blockIdx.x] = v;
-}
-
-// Sums the partials in a fixed order, decides whether the V-cycle loop goes on
-// and sets the while-node's condition.  Stopping rule: ||rho|| <= tol ||g||,
-// checked after every cycle; a non-finite norm or max_cycles ends the loop
-// with a status bit.
-template <bool kGraph>
-__global__ void k_finish_norm(const double *__restrict__ rpart, int nr, const double *__restrict__ gpart, int ng,
-                              DevState *ds, cudaGraphConditionalHandle h, double tol, int max_cycles) {
-    __shared__ double sh[32];
-    double sr = 0.0, sg = 0.0;
-    for (int k = threadIdx.x; k < nr; k += blockDim.x) sr += rpart[k];
-    for (int k = threadIdx.x; k < ng; k += blockDim.x) sg += gpart[k];
-    sr = block_sum(sr, sh);
-    sg = block_sum(sg, sh);
-    if (threadIdx.x != 0) return;
-    int cyc = ds->cycles + 1;
-    double rn = sqrt(sr), gn = sqrt(sg);
-    bool finite = isfinite(rn) && isfinite(gn);
-    unsigned int more = 0;
-    if (!finite) {
-        ds->status |= kStatusNonFinite;
-    } else if (rn <= tol * gn) {
-    } else if (cyc >= max_cycles) {
-        ds->status |= kStatusNoConv;
-    } else {
-        more = 1;
-    }
-    if (more) {
-        ds->cycles = cyc;
-    } else {
-        ds->cycles = 0;
-        ds->last_cycles = cyc;
-        ds->last_rel = gn > 0.0 ? rn / gn : (rn > 0.0 ? INFINITY : 0.0);
-        ds->log[ds->nsolves % kLogN] = cyc;
-        ds->nsolves += 1;
-    }
-    if (kGraph)
-        cudaGraphSetConditional(h, more);
-    else
-        ds->more = (int)more;
 }
 
 // Thom's wall vorticity, Eq. (25): -2 psi_adjacent / h^2 on every wall, minus
@@ -388,11 +379,20 @@ inline dim3 grid2(int nx, int ny, int bx, int by) { return dim3((nx + bx - 1) / 
 template <typename T>
 cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int colour, T beta) {
     dim3 blk(kBX, kBY);
+    bool relax = beta != T(1);
     if (op == 1) {
-        int n = N / 2;  // at most this many nodes of one parity per direction
-        k_smooth_colour<T, 1><<<grid2(n, n, kBX, kBY), blk, 0, s>>>(psi, g, N, P, colour, beta);
+        int n = N / 2;                      // at most this many nodes of one parity per direction
+        dim3 grid = grid2(n, (n + 1) / 2, kBX, kBY);  // two rows per thread
+        if (relax)
+            k_smooth_colour<T, 1, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+        else
+            k_smooth_colour<T, 1, false><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
     } else {
-        k_smooth_colour<T, 0><<<grid2(N / 2, N - 1, kBX, kBY), blk, 0, s>>>(psi, g, N, P, colour, beta);
+        dim3 grid = grid2(N / 2, N / 2, kBX, kBY);  // two rows per thread
+        if (relax)
+            k_smooth_colour<T, 0, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+        else
+            k_smooth_colour<T, 0, false><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
     }
     return cudaGetLastError();
 }
@@ -429,12 +429,13 @@ int assemble_blocks(int N) { return residual_norm_blocks(N); }
 int monitor_blocks(int N) { return ((N + 1 + kBX - 1) / kBX) * ((N + 1 + kBY - 1) / kBY); }
 
 template <typename T>
-cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials) {
+cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials,
+                                 FinishArgs fin) {
     dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
     if (op == 1)
-        k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials);
+        k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
     else
-        k_residual_norm<T, 0><<<grid, blk, 0, s>>>(psi, g, N, P, partials);
+        k_residual_norm<T, 0><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
     return cudaGetLastError();
 }
 
@@ -446,15 +447,6 @@ cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, dou
         k_assemble_rhs<1><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
     else
         k_assemble_rhs<0><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_finish_norm(cudaStream_t s, const double *rpart, int nr, const double *gpart, int ng, DevState *ds,
-                               cudaGraphConditionalHandle h, double tol, int max_cycles) {
-    if (h)
-        k_finish_norm<true><<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
-    else
-        k_finish_norm<false><<<1, 256, 0, s>>>(rpart, nr, gpart, ng, ds, h, tol, max_cycles);
     return cudaGetLastError();
 }
 
@@ -494,7 +486,8 @@ cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P) {
                                                      int);                                                           \
     template cudaError_t launch_prolong_correct<T>(cudaStream_t, T *, int, int, const T *, int);                     \
     template cudaError_t launch_coarsest<T>(cudaStream_t, int, T *, const T *, int, int, int, T);                    \
-    template cudaError_t launch_residual_norm<T>(cudaStream_t, int, const T *, const T *, int, int, double *);
+    template cudaError_t launch_residual_norm<T>(cudaStream_t, int, const T *, const T *, int, int, double *,         \
+                                                 FinishArgs);
 LCX_INSTANTIATE(double)
 LCX_INSTANTIATE(float)
 

@@ -39,9 +39,74 @@ __device__ __forceinline__ T gs_local(const T *sp, const T *sg, int c, int LP) {
 // Halo (x, y) a tile needs for a valid residual after nu sweeps.
 __host__ __device__ inline int halo_x(int op, int nu) { return op == 1 ? 4 * nu + 1 : 2 * nu + 1; }
 __host__ __device__ inline int halo_y(int op, int nu) { return 2 * nu + 1; }
+// Shared-memory tile geometry: LX x LY nodes, row pitch LP even and at least
+// LX + 1 (the pair loads of the last column read one element past it).
+__host__ __device__ inline int tile_lx(int TX, int op, int nu) { return TX + 2 * halo_x(op, nu) + 1; }
+__host__ __device__ inline int tile_ly(int TY, int nu) { return TY + 2 * halo_y(0, nu) + 1; }
+__host__ __device__ inline int tile_lp(int LX) { return (LX + 2) & ~1; }
+// Coarse tile staged by k_up: the coarse nodes under LX x LY fine nodes.
+__host__ __device__ inline int tile_lxc(int LX) { return LX / 2 + 3; }
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    typedef float2 type;
+};
+template <>
+struct Pair<double> {
+    typedef double2 type;
+};
+
+// W, P, E of local column x in one shared-memory row, read as two aligned
+// pairs (even offsets) so that the threads of a warp, which take every other
+// column, read contiguous memory without bank conflicts.
+template <typename T>
+__device__ __forceinline__ void row3(const T *row, int x, bool xodd, T &w, T &p, T &e) {
+    typedef typename Pair<T>::type P2;
+    if (xodd) {
+        P2 a = *reinterpret_cast<const P2 *>(row + x - 1), b = *reinterpret_cast<const P2 *>(row + x + 1);
+        w = a.x;
+        p = a.y;
+        e = b.x;
+    } else {
+        P2 a = *reinterpret_cast<const P2 *>(row + x - 2), b = *reinterpret_cast<const P2 *>(row + x);
+        w = a.y;
+        p = b.x;
+        e = b.y;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T mid1(const T *row, int x, bool xodd) {
+    typedef typename Pair<T>::type P2;
+    return xodd ? reinterpret_cast<const P2 *>(row + x - 1)->y : reinterpret_cast<const P2 *>(row + x)->x;
+}
+
+// Gauss-Seidel value of node (x, y) from pair loads; the operand order is the
+// one of gs_local, so the result is bit-identical.
+template <typename T, int OP>
+__device__ __forceinline__ T gs_pairs(const T *sp, const T *sg, int LP, int x, int y, bool xodd, T &pc) {
+    const T *r0 = sp + y * LP;
+    T w, p, e;
+    row3<T>(r0, x, xodd, w, p, e);
+    pc = p;
+    if (OP == 1) {
+        T nw, n, ne, sw, so, se;
+        row3<T>(r0 + LP, x, xodd, nw, n, ne);
+        row3<T>(r0 - LP, x, xodd, sw, so, se);
+        T n4 = (e + w) + (n + so);
+        T d4 = (ne + nw) + (se + sw);
+        return fma(T(0.2), n4, fma(T(0.05), d4, sg[y * LP + x]));
+    }
+    T n = mid1<T>(r0 + LP, x, xodd), so = mid1<T>(r0 - LP, x, xodd);
+    T n4 = (e + w) + (n + so);
+    return fma(T(0.25), n4, sg[y * LP + x]);
+}
 
 // One colour phase over the tile's updatable nodes: local [1, LX-2] x
-// [1, LY-2] intersected with the domain interior.  Block is 2-D.
+// [1, LY-2] intersected with the domain interior.  Block is 2-D with
+// blockDim.x = 32, so a warp works on one row.
 template <typename T, int OP>
 __device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, int gy0, int N, int colour,
                            T beta) {
@@ -49,6 +114,7 @@ __device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, 
         int pi = colour & 1, pj = colour >> 1;
         int x0 = ((gx0 + 1) & 1) == pi ? 1 : 2;
         int y0 = ((gy0 + 1) & 1) == pj ? 1 : 2;
+        bool xodd = x0 & 1;
         int nx = LX - 2 >= x0 ? (LX - 2 - x0) / 2 + 1 : 0;
         int ny = LY - 2 >= y0 ? (LY - 2 - y0) / 2 + 1 : 0;
         for (int yy = threadIdx.y; yy < ny; yy += blockDim.y) {
@@ -57,10 +123,10 @@ __device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, 
             for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
                 int x = x0 + 2 * xx, gi = gx0 + x;
                 if (gi < 1 || gi >= N) continue;
-                int c = y * LP + x;
-                T v = gs_local<T, OP>(sp, sg, c, LP);
-                if (beta != T(1)) v = fma(beta, v - sp[c], sp[c]);
-                sp[c] = v;
+                T pc;
+                T v = gs_pairs<T, OP>(sp, sg, LP, x, y, xodd, pc);
+                if (beta != T(1)) v = fma(beta, v - pc, pc);
+                sp[y * LP + x] = v;
             }
         }
     } else {
@@ -69,13 +135,14 @@ __device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, 
             int gj = gy0 + y;
             if (gj < 1 || gj >= N) continue;
             int x0 = ((gx0 + 1 + gj) & 1) == colour ? 1 : 2;
+            bool xodd = x0 & 1;
             for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
                 int x = x0 + 2 * xx, gi = gx0 + x;
                 if (x > LX - 2 || gi < 1 || gi >= N) continue;
-                int c = y * LP + x;
-                T v = gs_local<T, OP>(sp, sg, c, LP);
-                if (beta != T(1)) v = fma(beta, v - sp[c], sp[c]);
-                sp[c] = v;
+                T pc;
+                T v = gs_pairs<T, OP>(sp, sg, LP, x, y, xodd, pc);
+                if (beta != T(1)) v = fma(beta, v - pc, pc);
+                sp[y * LP + x] = v;
             }
         }
     }
@@ -89,6 +156,22 @@ __device__ void tile_sweeps(T *sp, const T *sg, int LP, int LX, int LY, int gx0,
             tile_phase<T, OP>(sp, sg, LP, LX, LY, gx0, gy0, N, col, beta);
             __syncthreads();
         }
+}
+
+// Asynchronous global -> shared copy of one element; an invalid element is
+// filled with zero (source size 0: nothing is read from src).
+template <typename T>
+__device__ __forceinline__ void cp_async_el(T *dst, const T *src, bool valid) {
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    int n = valid ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 __device__ __forceinline__ double block_sum2d(double v, double *sh) {
@@ -118,24 +201,25 @@ __global__ void __launch_bounds__(512)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sp = reinterpret_cast<T *>(smem_raw);
     int RX = halo_x(OP, nu), RY = halo_y(OP, nu);
-    int LX = TX + 2 * RX + 1, LY = TY + 2 * RY + 1, LP = LX;
+    int LX = tile_lx(TX, OP, nu), LY = tile_ly(TY, nu), LP = tile_lp(LX);
     T *sg = sp + LY * LP;
     int ox0 = 1 + blockIdx.x * TX, oy0 = 1 + blockIdx.y * TY;
     int gx0 = ox0 - RX, gy0 = oy0 - RY;
     for (int y = threadIdx.y; y < LY; y += blockDim.y) {
         int gj = gy0 + y;
-        for (int x = threadIdx.x; x < LX; x += blockDim.x) {
+        bool rowok = gj >= 0 && gj <= N;
+        for (int x = threadIdx.x; x < LP; x += blockDim.x) {
             int gi = gx0 + x;
-            T p = T(0), q = T(0);
-            if (gi >= 0 && gi <= N && gj >= 0 && gj <= N) {
-                size_t c = (size_t)gj * P + gi;
-                if (!zero_init) p = psi_in[c];
-                q = g[c];
-            }
-            sp[y * LP + x] = p;
-            sg[y * LP + x] = q;
+            bool ok = rowok && gi >= 0 && gi <= N && x < LX;
+            size_t c = ok ? (size_t)gj * P + gi : 0;
+            cp_async_el<T>(sg + y * LP + x, g + c, ok);
+            if (zero_init)
+                sp[y * LP + x] = T(0);
+            else
+                cp_async_el<T>(sp + y * LP + x, psi_in + c, ok);
         }
     }
+    cp_async_wait_all();
     __syncthreads();
     tile_sweeps<T, OP>(sp, sg, LP, LX, LY, gx0, gy0, N, nu, beta);
     // own psi out; residual (in place of g) on the owner region plus one node
@@ -170,45 +254,61 @@ __global__ void __launch_bounds__(512)
 // tile's sum of rho^2 over its owner nodes (partials != nullptr).  With
 // cor.psi64 set (the mixed-precision fine level) the smoothed correction is
 // not stored: it is added to the FP64 solution, psi64 += e, and the FP32
-// shadow of the new psi64 is written.
+// shadow of the new psi64 is written.  The coarse correction under the tile
+// is staged in shared memory first.
 template <typename T, int OP, int TX, int TY>
 __global__ void __launch_bounds__(512)
     k_up(const T *__restrict__ psi_in, const T *__restrict__ g, const T *__restrict__ ec, int Pc,
-         T *__restrict__ psi_out, int N, int P, int nu, T beta, double *__restrict__ partials, Correct64 cor) {
+         T *__restrict__ psi_out, int N, int P, int nu, T beta, double *__restrict__ partials, Correct64 cor,
+         FinishArgs fin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     T *sp = reinterpret_cast<T *>(smem_raw);
     int RX = halo_x(OP, nu), RY = halo_y(OP, nu);
-    int LX = TX + 2 * RX + 1, LY = TY + 2 * RY + 1, LP = LX;
-    T *sg = sp + LY * LP;
+    int LX = tile_lx(TX, OP, nu), LY = tile_ly(TY, nu), LP = tile_lp(LX);
+    int LXc = tile_lxc(LX), LYc = tile_lxc(LY);
+    T *sg = sp + LY * LP, *sc = sg + LY * LP;
     int ox0 = 1 + blockIdx.x * TX, oy0 = 1 + blockIdx.y * TY;
     int gx0 = ox0 - RX, gy0 = oy0 - RY;
+    int Ic0 = gx0 >> 1, Jc0 = gy0 >> 1, Nc = N / 2;  // floor, also for negative gx0
     for (int y = threadIdx.y; y < LY; y += blockDim.y) {
         int gj = gy0 + y;
+        bool rowok = gj >= 0 && gj <= N;
+        for (int x = threadIdx.x; x < LP; x += blockDim.x) {
+            int gi = gx0 + x;
+            bool ok = rowok && gi >= 0 && gi <= N && x < LX;
+            size_t c = ok ? (size_t)gj * P + gi : 0;
+            cp_async_el<T>(sp + y * LP + x, psi_in + c, ok);
+            cp_async_el<T>(sg + y * LP + x, g + c, ok);
+        }
+    }
+    for (int Y = threadIdx.y; Y < LYc; Y += blockDim.y) {
+        int J = Jc0 + Y;
+        for (int X = threadIdx.x; X < LXc; X += blockDim.x) {
+            int I = Ic0 + X;
+            bool ok = J >= 0 && J <= Nc && I >= 0 && I <= Nc;
+            cp_async_el<T>(sc + Y * LXc + X, ec + (ok ? (size_t)J * Pc + I : 0), ok);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int y = threadIdx.y; y < LY; y += blockDim.y) {
+        int gj = gy0 + y;
+        if (gj < 1 || gj >= N) continue;
         for (int x = threadIdx.x; x < LX; x += blockDim.x) {
             int gi = gx0 + x;
-            T p = T(0), q = T(0);
-            if (gi >= 0 && gi <= N && gj >= 0 && gj <= N) {
-                size_t c = (size_t)gj * P + gi;
-                p = psi_in[c];
-                q = g[c];
-                if (gi >= 1 && gi < N && gj >= 1 && gj < N) {
-                    int I = gi >> 1, J = gj >> 1;
-                    size_t cc = (size_t)J * Pc + I;
-                    T e;
-                    if (!(gi & 1) && !(gj & 1))
-                        e = ec[cc];
-                    else if ((gi & 1) && !(gj & 1))
-                        e = T(0.5) * (ec[cc] + ec[cc + 1]);
-                    else if (!(gi & 1) && (gj & 1))
-                        e = T(0.5) * (ec[cc] + ec[cc + Pc]);
-                    else
-                        e = T(0.25) * ((ec[cc] + ec[cc + 1]) + (ec[cc + Pc] + ec[cc + Pc + 1]));
-                    p += e;
-                }
-            }
-            sp[y * LP + x] = p;
-            sg[y * LP + x] = q;
+            if (gi < 1 || gi >= N) continue;
+            int cc = ((gj >> 1) - Jc0) * LXc + ((gi >> 1) - Ic0);
+            T e;
+            if (!(gi & 1) && !(gj & 1))
+                e = sc[cc];
+            else if ((gi & 1) && !(gj & 1))
+                e = T(0.5) * (sc[cc] + sc[cc + 1]);
+            else if (!(gi & 1) && (gj & 1))
+                e = T(0.5) * (sc[cc] + sc[cc + LXc]);
+            else
+                e = T(0.25) * ((sc[cc] + sc[cc + 1]) + (sc[cc + LXc] + sc[cc + LXc + 1]));
+            sp[y * LP + x] += e;
         }
     }
     __syncthreads();
@@ -238,49 +338,41 @@ __global__ void __launch_bounds__(512)
     if (partials) {
         acc = block_sum2d(acc, red);
         if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = acc;
+        if (fin.enabled) finish_if_last(partials, fin);
     }
 }
 
 // ---------------------------------------------------------------------------
 // A V-cycle over levels N0, N0/2, ..., down to 2 or 3 intervals, in one block
-// with every level in shared memory (pitch N_k + 1).  g_in: right-hand side of
+// with every level in shared memory (level k: psi then g, pitch N_k + 1,
+// starting at offset sum_{k'<k} 2 (N_k' + 1)^2).  g_in: right-hand side of
 // the top level; psi_warm: its initial guess (nullptr = zero); psi_out: where
 // the top level's result goes; partial: if set, the sum of rho^2 of the top
-// level after the cycle.
+// level after the cycle (and the end-of-cycle decision if fin.enabled).
 template <typename T, int OP>
-__device__ void cs_phase(T *sp, const T *sg, int n, int colour, T beta) {
-    int LP = n + 1, m = n - 1;
-    int tid = threadIdx.x, nt = blockDim.x;
-    if (OP == 1) {
-        int pi = colour & 1, pj = colour >> 1;
-        int x0 = pi ? 1 : 2, y0 = pj ? 1 : 2;
-        int nx = m >= x0 ? (m - x0) / 2 + 1 : 0, ny = m >= y0 ? (m - y0) / 2 + 1 : 0;
-        for (int k = tid; k < nx * ny; k += nt) {
-            int x = x0 + 2 * (k % nx), y = y0 + 2 * (k / nx);
-            int c = y * LP + x;
-            T v = gs_local<T, OP>(sp, sg, c, LP);
-            if (beta != T(1)) v = fma(beta, v - sp[c], sp[c]);
-            sp[c] = v;
-        }
-    } else {
-        int nx = m / 2 + 1;
-        for (int k = tid; k < nx * m; k += nt) {
-            int y = 1 + k / nx;
-            int x = (((1 + y) & 1) == colour ? 1 : 2) + 2 * (k % nx);
-            if (x > m) continue;
-            int c = y * LP + x;
-            T v = gs_local<T, OP>(sp, sg, c, LP);
-            if (beta != T(1)) v = fma(beta, v - sp[c], sp[c]);
-            sp[c] = v;
-        }
-    }
+__device__ __forceinline__ void cs_update(T *sp, const T *sg, int c, int LP, T beta) {
+    T v = gs_local<T, OP>(sp, sg, c, LP);
+    if (beta != T(1)) v = fma(beta, v - sp[c], sp[c]);
+    sp[c] = v;
 }
 
 template <typename T, int OP>
 __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
+    int LP = n + 1, m = n - 1;
     for (int s = 0; s < nu; ++s)
         for (int col = 0; col < (OP == 1 ? 4 : 2); ++col) {
-            cs_phase<T, OP>(sp, sg, n, col, beta);
+            if (OP == 1) {
+                int x0 = (col & 1) ? 1 : 2, y0 = (col >> 1) ? 1 : 2;
+                for (int y = y0 + 2 * (int)threadIdx.y; y <= m; y += 2 * blockDim.y)
+                    for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
+                        cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+            } else {
+                for (int y = 1 + threadIdx.y; y <= m; y += blockDim.y) {
+                    int x0 = ((1 + y) & 1) == col ? 1 : 2;
+                    for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
+                        cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+                }
+            }
             __syncthreads();
         }
 }
@@ -288,58 +380,62 @@ __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
 template <typename T, int OP>
 __global__ void __launch_bounds__(1024)
     k_coarse(const T *__restrict__ g_in, int Pg, const T *__restrict__ psi_warm, T *__restrict__ psi_out, int Po,
-             int N0, int nl, int nu1, int nu2, int nuc, T beta, double *__restrict__ partial) {
+             int N0, int nl, int nu1, int nu2, int nuc, T beta, double *__restrict__ partial, FinishArgs fin) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     T *base = reinterpret_cast<T *>(smem_raw);
-    T *sp[kMaxLevels], *sg[kMaxLevels];
-    int off = 0;
-    for (int k = 0; k < nl; ++k) {
-        int n = N0 >> k, sz = (n + 1) * (n + 1);
-        sp[k] = base + off;
-        sg[k] = base + off + sz;
-        off += 2 * sz;
-    }
-    T *sr = base + off;  // residual scratch, (N0+1)^2
-    int tid = threadIdx.x, nt = blockDim.x;
-    for (int k = tid; k < off; k += nt) base[k] = T(0);
+    int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
+    int tid = ty * bx + tx, nt = bx * by;
+    int total = 0;
+    for (int k = 0; k < nl; ++k) total += 2 * ((N0 >> k) + 1) * ((N0 >> k) + 1);
+    T *sr = base + total;  // residual scratch, (N0+1)^2
+    for (int q = tid; q < total; q += nt) base[q] = T(0);
     __syncthreads();
     int L0 = N0 + 1;
-    for (int k = tid; k < L0 * L0; k += nt) {
-        int x = k % L0, y = k / L0;
-        if (x >= 1 && x < N0 && y >= 1 && y < N0) {
-            sg[0][k] = g_in[(size_t)y * Pg + x];
-            if (psi_warm) sp[0][k] = psi_warm[(size_t)y * Po + x];
+    for (int y = 1 + ty; y < N0; y += by)
+        for (int x = 1 + tx; x < N0; x += bx) {
+            base[L0 * L0 + y * L0 + x] = g_in[(size_t)y * Pg + x];
+            if (psi_warm) base[y * L0 + x] = psi_warm[(size_t)y * Po + x];
         }
-    }
     __syncthreads();
+    // down
+    int off = 0;
     for (int k = 0; k + 1 < nl; ++k) {
         int n = N0 >> k, LP = n + 1, nc = n / 2, LPc = nc + 1;
-        cs_sweeps<T, OP>(sp[k], sg[k], n, nu1, beta);
-        for (int q = tid; q < LP * LP; q += nt) {
-            int x = q % LP, y = q / LP;
-            sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? gs_local<T, OP>(sp[k], sg[k], q, LP) - sp[k][q] : T(0);
-        }
+        T *sp = base + off, *sg = sp + LP * LP;
+        T *spc = sg + LP * LP, *sgc = spc + LPc * LPc;
+        cs_sweeps<T, OP>(sp, sg, n, nu1, beta);
+        for (int y = ty; y <= n; y += by)
+            for (int x = tx; x <= n; x += bx) {
+                int q = y * LP + x;
+                sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? gs_local<T, OP>(sp, sg, q, LP) - sp[q] : T(0);
+            }
         __syncthreads();
-        for (int q = tid; q < LPc * LPc; q += nt) {
-            int X = q % LPc, Y = q / LPc;
-            if (X >= 1 && X < nc && Y >= 1 && Y < nc) {
+        for (int Y = 1 + ty; Y < nc; Y += by)
+            for (int X = 1 + tx; X < nc; X += bx) {
                 const T *r = sr + (2 * Y) * LP + 2 * X;
                 T e4 = (r[1] + r[-1]) + (r[LP] + r[-LP]);
                 T d4 = (r[LP + 1] + r[LP - 1]) + (r[-LP + 1] + r[-LP - 1]);
-                sg[k + 1][q] = fma(T(0.5), e4, fma(T(0.25), d4, r[0]));
+                sgc[Y * LPc + X] = fma(T(0.5), e4, fma(T(0.25), d4, r[0]));
+                spc[Y * LPc + X] = T(0);
             }
-            sp[k + 1][q] = T(0);
-        }
         __syncthreads();
+        off += 2 * LP * LP;
     }
-    cs_sweeps<T, OP>(sp[nl - 1], sg[nl - 1], N0 >> (nl - 1), nuc, beta);
+    {
+        int n = N0 >> (nl - 1), LP = n + 1;
+        T *sp = base + off, *sg = sp + LP * LP;
+        // with one unknown and beta = 1 a single sweep is already exact
+        cs_sweeps<T, OP>(sp, sg, n, (n == 2 && beta == T(1)) ? 1 : nuc, beta);
+    }
+    // up
     for (int k = nl - 2; k >= 0; --k) {
         int n = N0 >> k, LP = n + 1, LPc = n / 2 + 1;
-        const T *ec = sp[k + 1];
-        for (int q = tid; q < LP * LP; q += nt) {
-            int i = q % LP, j = q / LP;
-            if (i >= 1 && i < n && j >= 1 && j < n) {
+        off -= 2 * LP * LP;
+        T *sp = base + off, *sg = sp + LP * LP;
+        const T *ec = sg + LP * LP;
+        for (int j = 1 + ty; j < n; j += by)
+            for (int i = 1 + tx; i < n; i += bx) {
                 int I = i >> 1, J = j >> 1, cc = J * LPc + I;
                 T e;
                 if (!(i & 1) && !(j & 1))
@@ -350,42 +446,35 @@ __global__ void __launch_bounds__(1024)
                     e = T(0.5) * (ec[cc] + ec[cc + LPc]);
                 else
                     e = T(0.25) * ((ec[cc] + ec[cc + 1]) + (ec[cc + LPc] + ec[cc + LPc + 1]));
-                sp[k][q] += e;
+                sp[j * LP + i] += e;
             }
-        }
         __syncthreads();
-        cs_sweeps<T, OP>(sp[k], sg[k], n, nu2, beta);
+        cs_sweeps<T, OP>(sp, sg, n, nu2, beta);
     }
     double acc = 0.0;
-    for (int k = tid; k < L0 * L0; k += nt) {
-        int x = k % L0, y = k / L0;
-        if (x >= 1 && x < N0 && y >= 1 && y < N0) {
-            psi_out[(size_t)y * Po + x] = sp[0][k];
+    for (int y = 1 + ty; y < N0; y += by)
+        for (int x = 1 + tx; x < N0; x += bx) {
+            int q = y * L0 + x;
+            psi_out[(size_t)y * Po + x] = base[q];
             if (partial) {
-                double r = (double)(gs_local<T, OP>(sp[0], sg[0], k, L0) - sp[0][k]);
+                double r = (double)(gs_local<T, OP>(base, base + L0 * L0, q, L0) - base[q]);
                 acc += r * r;
             }
         }
-    }
     if (partial) {
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        int lane = tid & 31, warp = tid >> 5;
-        if (lane == 0) red[warp] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            acc = lane < (nt + 31) / 32 ? red[lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-            if (lane == 0) partial[0] = acc;
-        }
+        acc = block_sum2d(acc, red);
+        if (tid == 0) partial[0] = acc;
+        if (fin.enabled) finish_if_last(partial, fin);
     }
 }
 
 constexpr int kTBX = 32, kTBY = 16;  // 512 threads per tile block
 
+// Shared memory of a tile kernel: psi and g tiles, plus k_up's coarse tile.
 template <typename T, int TX, int TY>
 size_t down_smem(int op, int nu) {
-    int LX = TX + 2 * halo_x(op, nu) + 1, LY = TY + 2 * halo_y(op, nu) + 1;
-    return 2 * (size_t)LX * LY * sizeof(T);
+    int LX = tile_lx(TX, op, nu), LY = tile_ly(TY, nu), LP = tile_lp(LX);
+    return (2 * (size_t)LY * LP + (size_t)tile_lxc(LX) * tile_lxc(LY)) * sizeof(T);
 }
 
 template <typename T, int OP, int TX, int TY>
@@ -400,50 +489,96 @@ cudaError_t down_t(cudaStream_t s, const T *psi_in, int zero_init, const T *g, T
 
 template <typename T, int OP, int TX, int TY>
 cudaError_t up_t(cudaStream_t s, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N, int P, int nu,
-                 T beta, double *partials, Correct64 cor) {
+                 T beta, double *partials, Correct64 cor, FinishArgs fin) {
     size_t sm = down_smem<T, TX, TY>(OP, nu);
     auto kern = k_up<T, OP, TX, TY>;
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
-    kern<<<grid, dim3(kTBX, kTBY), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor);
+    kern<<<grid, dim3(kTBX, kTBY), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
     return cudaGetLastError();
+}
+
+constexpr int kShapeTX[4] = {128, 64, 32, 16};
+constexpr int kShapeTY[4] = {64, 64, 32, 16};
+
+}  // namespace
+
+int tiles_of(int N, int shape) {
+    return ((N - 1 + kShapeTX[shape] - 1) / kShapeTX[shape]) * ((N - 1 + kShapeTY[shape] - 1) / kShapeTY[shape]);
+}
+
+size_t tile_smem_bytes(int shape, int op, int nu, int elem) {
+    int LX = tile_lx(kShapeTX[shape], op, nu), LY = tile_ly(kShapeTY[shape], nu), LP = tile_lp(LX);
+    return (2 * (size_t)LY * LP + (size_t)tile_lxc(LX) * tile_lxc(LY)) * elem;
+}
+
+// Picks the tile shape of a level by a simple cost model.  FP64 tiles are
+// bound by the SM's FP64 pipe, which the blocks resident on one SM share, so
+// a launch costs (tiles per SM) x (nodes of a tile including its recomputed
+// halo); FP32 tiles are latency-bound, so a launch costs (waves of resident
+// blocks) x (a fixed barrier-chain latency + a small per-node term).
+int tile_shape_for(int N, int op, int nu, int elem, int force) {
+    if (force >= 0 && force < 4 && tile_smem_bytes(force, op, nu, elem) <= kMaxSmem - 1024) return force;
+    const int sms = 152;
+    double best = 1e300;
+    int pick = 3;
+    for (int sh = 0; sh < 4; ++sh) {
+        size_t sm = tile_smem_bytes(sh, op, nu, elem);
+        if (sm > kMaxSmem - 1024) continue;
+        int bps = (int)((kMaxSmem - 1024) / sm);
+        if (bps > 4) bps = 4;
+        int LX = tile_lx(kShapeTX[sh], op, nu), LY = tile_ly(kShapeTY[sh], nu);
+        int nt = tiles_of(N, sh);
+        double cost;
+        if (elem == 8)
+            cost = (double)((nt + sms - 1) / sms) * ((double)LX * LY * (nu + 1) + 1500.0);
+        else
+            cost = (double)((nt + sms * bps - 1) / (sms * bps)) * (0.08 * LX * LY * (nu + 1) + 3000.0);
+        if (cost < best) {
+            best = cost;
+            pick = sh;
+        }
+    }
+    return pick;
+}
+
+namespace {
+
+template <typename T, int OP>
+cudaError_t down_shape(cudaStream_t s, int shape, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
+                       T *gc, int Pc, int nu, T beta) {
+    switch (shape) {
+        case 0: return down_t<T, OP, 128, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        case 1: return down_t<T, OP, 64, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        case 2: return down_t<T, OP, 32, 32>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        default: return down_t<T, OP, 16, 16>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+    }
+}
+
+template <typename T, int OP>
+cudaError_t up_shape(cudaStream_t s, int shape, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
+                     int P, int nu, T beta, double *partials, Correct64 cor, FinishArgs fin) {
+    switch (shape) {
+        case 0: return up_t<T, OP, 128, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        case 1: return up_t<T, OP, 64, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        case 2: return up_t<T, OP, 32, 32>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        default: return up_t<T, OP, 16, 16>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+    }
 }
 
 }  // namespace
 
-// Tile shape per level: large tiles (fewer recomputed halo nodes) where the
-// level has enough of them to fill the GPU, small ones otherwise.
-bool use_big_tiles(int N) { return ((N - 1 + 127) / 128) * ((N - 1 + 63) / 64) >= 120; }
-
-int tiles_of(int N) {
-    return use_big_tiles(N) ? ((N - 1 + 127) / 128) * ((N - 1 + 63) / 64) : ((N - 1 + 31) / 32) * ((N - 1 + 31) / 32);
-}
-
-size_t tile_smem_bytes(int N, int op, int nu, int elem) {
-    int TX = use_big_tiles(N) ? 128 : 32, TY = use_big_tiles(N) ? 64 : 32;
-    int LX = TX + 2 * halo_x(op, nu) + 1, LY = TY + 2 * halo_y(op, nu) + 1;
-    return 2 * (size_t)LX * LY * elem;
+template <typename T>
+cudaError_t launch_down(cudaStream_t s, int shape, int op, const T *psi_in, int zero_init, const T *g, T *psi_out,
+                        int N, int P, T *gc, int Pc, int nu, T beta) {
+    if (op == 1) return down_shape<T, 1>(s, shape, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+    return down_shape<T, 0>(s, shape, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
 }
 
 template <typename T>
-cudaError_t launch_down(cudaStream_t s, int op, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
-                        T *gc, int Pc, int nu, T beta) {
-    bool big = use_big_tiles(N);
-    if (op == 1)
-        return big ? down_t<T, 1, 128, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta)
-                   : down_t<T, 1, 32, 32>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
-    return big ? down_t<T, 0, 128, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta)
-               : down_t<T, 0, 32, 32>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
-}
-
-template <typename T>
-cudaError_t launch_up(cudaStream_t s, int op, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
-                      int P, int nu, T beta, double *partials, Correct64 cor) {
-    bool big = use_big_tiles(N);
-    if (op == 1)
-        return big ? up_t<T, 1, 128, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor)
-                   : up_t<T, 1, 32, 32>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor);
-    return big ? up_t<T, 0, 128, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor)
-               : up_t<T, 0, 32, 32>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor);
+cudaError_t launch_up(cudaStream_t s, int shape, int op, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out,
+                      int N, int P, int nu, T beta, double *partials, Correct64 cor, FinishArgs fin) {
+    if (op == 1) return up_shape<T, 1>(s, shape, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+    return up_shape<T, 0>(s, shape, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
 }
 
 size_t coarse_smem_bytes(int N0, int nl, int elem) {
@@ -455,11 +590,11 @@ size_t coarse_smem_bytes(int N0, int nl, int elem) {
 
 template <typename T>
 cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T *psi_warm, T *psi_out, int Po, int N0,
-                          int nl, int nu1, int nu2, int nuc, T beta, double *partial) {
+                          int nl, int nu1, int nu2, int nuc, T beta, double *partial, FinishArgs fin) {
     size_t sm = coarse_smem_bytes(N0, nl, sizeof(T));
     auto kern = op == 1 ? k_coarse<T, 1> : k_coarse<T, 0>;
-    int threads = sizeof(T) == 8 ? 512 : 1024;
-    kern<<<1, threads, sm, s>>>(g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial);
+    dim3 blk(32, sizeof(T) == 8 ? 16 : 32);
+    kern<<<1, blk, sm, s>>>(g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial, fin);
     return cudaGetLastError();
 }
 
@@ -467,11 +602,13 @@ cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T
 // any launch or graph capture.
 template <typename T>
 static cudaError_t set_attrs_t() {
-    const void *k[] = {(const void *)k_down<T, 0, 128, 64>, (const void *)k_down<T, 1, 128, 64>,
-                       (const void *)k_down<T, 0, 32, 32>,  (const void *)k_down<T, 1, 32, 32>,
-                       (const void *)k_up<T, 0, 128, 64>,   (const void *)k_up<T, 1, 128, 64>,
-                       (const void *)k_up<T, 0, 32, 32>,    (const void *)k_up<T, 1, 32, 32>,
-                       (const void *)k_coarse<T, 0>,        (const void *)k_coarse<T, 1>};
+    const void *k[] = {
+        (const void *)k_down<T, 0, 128, 64>, (const void *)k_down<T, 1, 128, 64>, (const void *)k_down<T, 0, 64, 64>,
+        (const void *)k_down<T, 1, 64, 64>,  (const void *)k_down<T, 0, 32, 32>,  (const void *)k_down<T, 1, 32, 32>,
+        (const void *)k_down<T, 0, 16, 16>,  (const void *)k_down<T, 1, 16, 16>,  (const void *)k_up<T, 0, 128, 64>,
+        (const void *)k_up<T, 1, 128, 64>,   (const void *)k_up<T, 0, 64, 64>,    (const void *)k_up<T, 1, 64, 64>,
+        (const void *)k_up<T, 0, 32, 32>,    (const void *)k_up<T, 1, 32, 32>,    (const void *)k_up<T, 0, 16, 16>,
+        (const void *)k_up<T, 1, 16, 16>,    (const void *)k_coarse<T, 0>,        (const void *)k_coarse<T, 1>};
     for (const void *f : k) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
         if (e != cudaSuccess) return e;
@@ -485,11 +622,12 @@ cudaError_t init_mg_kernel_attributes() {
 }
 
 #define LCX_MG_INSTANTIATE(T)                                                                                          \
-    template cudaError_t launch_down<T>(cudaStream_t, int, const T *, int, const T *, T *, int, int, T *, int, int, T); \
-    template cudaError_t launch_up<T>(cudaStream_t, int, const T *, const T *, const T *, int, T *, int, int, int, T,   \
-                                      double *, Correct64);                                                           \
+    template cudaError_t launch_down<T>(cudaStream_t, int, int, const T *, int, const T *, T *, int, int, T *, int,   \
+                                        int, T);                                                                      \
+    template cudaError_t launch_up<T>(cudaStream_t, int, int, const T *, const T *, const T *, int, T *, int, int,     \
+                                      int, T, double *, Correct64, FinishArgs);                                       \
     template cudaError_t launch_coarse<T>(cudaStream_t, int, const T *, int, const T *, T *, int, int, int, int, int,  \
-                                          int, T, double *);
+                                          int, T, double *, FinishArgs);
 LCX_MG_INSTANTIATE(double)
 LCX_MG_INSTANTIATE(float)
 

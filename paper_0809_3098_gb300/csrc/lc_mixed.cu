@@ -42,7 +42,7 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
 template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual64_to32(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
-                      float *__restrict__ r32, int P32, double *__restrict__ partials) {
+                      float *__restrict__ r32, int P32, double *__restrict__ partials, FinishArgs fin) {
     __shared__ double sh[32];
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = v;
+    if (fin.enabled) finish_if_last(partials, fin);
 }
 
 __global__ void __launch_bounds__(kBX *kBY)
@@ -165,11 +166,13 @@ __global__ void k_to32(const double *__restrict__ src, int P64, float *__restric
 }  // namespace
 
 cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
-                                   float *r32, int P32, double *partials) {
+                                   float *r32, int P32, double *partials, FinishArgs fin) {
     if (op == 1)
-        k_residual64_to32<1><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials);
+        k_residual64_to32<1><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials,
+                                                                              fin);
     else
-        k_residual64_to32<0><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials);
+        k_residual64_to32<0><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials,
+                                                                              fin);
     return cudaGetLastError();
 }
 

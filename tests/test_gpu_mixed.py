@@ -98,3 +98,13 @@ def test_mixed_errors_reported():
     with pytest.raises(lc.LCError) as e:
         g.synchronize()
     assert e.value.code == lc.LC_ERR_NOCONV
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2, 3])
+def test_mixed_tile_shapes_bitwise_identical(shape):
+    N = 384
+    a = lc.Cavity(N, 5000.0, precision=MIXED, tile_shape=shape)
+    b = lc.Cavity(N, 5000.0, precision=MIXED, tile_shape=2)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())

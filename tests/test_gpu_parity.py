@@ -214,6 +214,9 @@ MODES = {
     "tiles": dict(blocked=1, fine_phases=0, coarse_max=2),
     "tiles+fine-phases": dict(blocked=1, fine_phases=1, coarse_max=4),
     "coarse-block": dict(blocked=1, fine_phases=0, coarse_max=64),
+    "tiles128x64": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0),
+    "tiles64x64": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1),
+    "tiles16x16": dict(blocked=1, fine_phases=0, coarse_max=2, tile_shape=3),
 }
 
 
