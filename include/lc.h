@@ -207,6 +207,59 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * change the state: use only on a context whose state no longer matters. */
 int lc_bench_kernel(lc_ctx *ctx, int kernel, int reps, double out[4]);
 
+/* ---- Batched engine ------------------------------------------------------
+ * Many cavities of different sizes and Reynolds numbers advanced together:
+ * each step is one CUDA graph launch whose kernels cover every cavity (a
+ * table of per-cavity block ranges maps each thread block to its cavity and
+ * tile).  Every cavity runs the mixed-precision step of the single-cavity
+ * functions (LC_PREC_MIXED) with its own Poisson stopping rule: a cavity that
+ * has converged stops iterating while the others go on, so each cavity makes
+ * exactly the V-cycles it would make alone and its result is bit-identical to
+ * a single-cavity context with the same options. */
+typedef struct lc_batch lc_batch;
+
+/* count (1..256) cavities; N[c] must be 2^k or 3*2^k in 128..8192; Re[c] > 0;
+ * dt may be NULL or hold dt[c] <= 0 to apply dt = 0.25 min(h, Re h^2 / 4);
+ * tol as lc_create; precision must be LC_PREC_MIXED.  All cavities start at
+ * rest (as lc_create).  NULL on error (lc_last_error). */
+lc_batch *lc_batch_create(int count, const int *N, const double *Re, const double *dt, double tol, int precision);
+void lc_batch_destroy(lc_batch *b);
+
+/* Options as lc_set_option: "op", "coarse_max" (8..64) [before first use],
+ * "nu1", "nu2" (1..4), "nuc", "beta", "max_cycles", "U", "advect", "graph". */
+int lc_batch_set_option(lc_batch *b, const char *key, double value);
+int lc_batch_set_stream(lc_batch *b, void *cuda_stream);
+size_t lc_batch_workspace_bytes(int count, const int *N, int precision);
+int lc_batch_bind_workspace(lc_batch *b, void *dev_ptr, size_t bytes);
+
+/* Enqueues nsteps steps of every cavity (one graph launch per step). */
+int lc_batch_step(lc_batch *b, int nsteps);
+
+/* Copies cavity c's psi (field 0) or omega (field 1), (N[c]+1)^2 FP64 values
+ * in the host layout of this header.  Waits for the stream and reports the
+ * first pending device error of any cavity. */
+int lc_batch_get(lc_batch *b, int cavity, int field, double *host_out, size_t n_elems);
+
+/* Installs cavity c's state as lc_set_state does. */
+int lc_batch_set_state(lc_batch *b, int cavity, const double *psi, const double *omega);
+
+/* V-cycle counts of cavity c's solves, as lc_cycle_log. */
+int lc_batch_cycle_log(lc_batch *b, int cavity, int *out, size_t max, size_t *n_out);
+int lc_batch_synchronize(lc_batch *b);
+
+/* out[0] = N, out[1] = Re, out[2] = dt, out[3] = multigrid levels, out[4] =
+ * first level of the one-block coarse cycle, out[5] = steps taken, out[6] =
+ * tile shape of level 0, out[7] = workspace bytes. */
+int lc_batch_info(lc_batch *b, int cavity, double out[8]);
+
+/* Autotuner: for every tile level, times `reps` launches of the batch's
+ * pre- and post-smoothing tile kernels in each tile shape (128x64, 64x64,
+ * 32x32, 16x16 owned nodes; those that fit in shared memory) on the current
+ * state, keeps the fastest, and writes the chosen shape per level to
+ * shapes_out[0..max_levels) (-1 past the last tile level).  The tile shape
+ * does not change any result (bit-identical); the state is restored. */
+int lc_batch_autotune(lc_batch *b, int reps, int *shapes_out, int max_levels);
+
 /* Largest N accepted by lc_monitor_noalloc: the size of its fixed scratch. */
 #define LC_NOALLOC_MAX_N 8192
 

@@ -207,6 +207,88 @@ cudaError_t launch_thom_mixed(cudaStream_t s, const double *psi64, double *const
                               int P64, int P32, double U, int profile);
 cudaError_t launch_to32(cudaStream_t s, const double *src, int P64, float *dst, int P32, int N);
 
+// ---- batched engine (lc_batch.cu host side; kernels in lc_mg.cu and lc_mixed.cu)
+constexpr int kMaxBatch = 256;
+
+// One cavity of a batch (device memory; the solve state fields change on the
+// device).  Mixed precision: the fine level holds psi64/g64 (FP64) and the
+// FP32 correction hierarchy eA/eB/g32 (g32[0] is the FP32 residual).
+struct BatchCav {
+    int N, nlev, lc;  // intervals, multigrid levels, first level of the one-block coarse cycle
+    int P[kMaxLevels];
+    double Re, dt;
+    double *psi64, *g64;
+    float *psi32;
+    float *eA[kMaxLevels], *eB[kMaxLevels], *g32[kMaxLevels];
+    double *W[4];  // W0, Wa, Wb, ACC
+    float *Ws[3];  // FP32 shadows of W0, Wa, Wb
+    int *log;      // cycles per solve, ring of kLogN
+    // solve state
+    int active, cycles, status, last_cycles;
+    unsigned int arrive;
+    int pad;
+    double last_rel;
+    unsigned long long nsolves;
+};
+
+// Block ranges of one batched launch: cavity c owns blocks [start[c], start[c+1])
+// laid out as gx[c] blocks per row.
+struct BatchRange {
+    int count;
+    int start[kMaxBatch + 1];
+    int gx[kMaxBatch];
+};
+
+// Batch-wide loop state.
+struct BatchState {
+    unsigned int cav_arrive;  // cavities whose decision is taken this cycle
+    int more;                 // eager mode: 1 if any cavity's loop goes on
+    int any_status;
+    int pad;
+};
+
+#ifdef __CUDACC__
+// Cavity and block coordinates of this block in a batched launch.
+__device__ __forceinline__ int batch_locate(const BatchRange *r, int &bx, int &by) {
+    int b = blockIdx.x, lo = 0, hi = r->count;  // start[lo] <= b < start[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (r->start[mid] <= b) lo = mid;
+        else hi = mid;
+    }
+    int local = b - r->start[lo];
+    bx = local % r->gx[lo];
+    by = local / r->gx[lo];
+    return lo;
+}
+#endif
+
+struct BatchFinish {
+    int enabled;
+    double tol;
+    int max_cycles;
+    cudaGraphConditionalHandle h;
+    BatchState *bs;
+};
+
+// batched kernels
+template <typename T>
+cudaError_t launch_down_batch(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
+                              int nblocks, int nu, T beta);
+template <typename T>
+cudaError_t launch_up_batch(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
+                            int nblocks, int nu, T beta);
+cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count, int smem, int nu1, int nu2, int nuc,
+                                float beta);
+cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
+                               int advect);
+cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
+                                  double *gpart);
+cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks,
+                                  double *rpart, const double *gpart, BatchFinish fin);
+cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U);
+cudaError_t launch_to32_batch(cudaStream_t s, BatchCav *cav, int c);
+
 // Sets the calling thread's lc_last_error() message.
 void set_last_error(const char *msg);
 

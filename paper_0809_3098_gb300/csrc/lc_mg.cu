@@ -195,15 +195,14 @@ __device__ __forceinline__ double block_sum2d(double v, double *sh) {
 // coarse nodes I with 2I inside that range.  zero_init: psi starts at 0 (the
 // coarse-level correction), psi_in is not read.
 template <typename T, int OP, int TX, int TY>
-__global__ void __launch_bounds__(512)
-    k_down(const T *__restrict__ psi_in, int zero_init, const T *__restrict__ g, T *__restrict__ psi_out, int N,
-           int P, T *__restrict__ gc, int Pc, int nu, T beta) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void down_body(int bx, int by, const T *__restrict__ psi_in, int zero_init,
+                                          const T *__restrict__ g, T *__restrict__ psi_out, int N, int P,
+                                          T *__restrict__ gc, int Pc, int nu, T beta, unsigned char *smem_raw) {
     T *sp = reinterpret_cast<T *>(smem_raw);
     int RX = halo_x(OP, nu), RY = halo_y(OP, nu);
     int LX = tile_lx(TX, OP, nu), LY = tile_ly(TY, nu), LP = tile_lp(LX);
     T *sg = sp + LY * LP;
-    int ox0 = 1 + blockIdx.x * TX, oy0 = 1 + blockIdx.y * TY;
+    int ox0 = 1 + bx * TX, oy0 = 1 + by * TY;
     int gx0 = ox0 - RX, gy0 = oy0 - RY;
     for (int y = threadIdx.y; y < LY; y += blockDim.y) {
         int gj = gy0 + y;
@@ -250,6 +249,14 @@ __global__ void __launch_bounds__(512)
     }
 }
 
+template <typename T, int OP, int TX, int TY>
+__global__ void __launch_bounds__(512)
+    k_down(const T *__restrict__ psi_in, int zero_init, const T *__restrict__ g, T *__restrict__ psi_out, int N,
+           int P, T *__restrict__ gc, int Pc, int nu, T beta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    down_body<T, OP, TX, TY>(blockIdx.x, blockIdx.y, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta, smem_raw);
+}
+
 // Prolongation + correction + post-smoothing; on the fine level also the
 // tile's sum of rho^2 over its owner nodes (partials != nullptr).  With
 // cor.psi64 set (the mixed-precision fine level) the smoothed correction is
@@ -257,18 +264,15 @@ __global__ void __launch_bounds__(512)
 // shadow of the new psi64 is written.  The coarse correction under the tile
 // is staged in shared memory first.
 template <typename T, int OP, int TX, int TY>
-__global__ void __launch_bounds__(512)
-    k_up(const T *__restrict__ psi_in, const T *__restrict__ g, const T *__restrict__ ec, int Pc,
-         T *__restrict__ psi_out, int N, int P, int nu, T beta, double *__restrict__ partials, Correct64 cor,
-         FinishArgs fin) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+__device__ __forceinline__ double up_body(int bx, int by, const T *__restrict__ psi_in, const T *__restrict__ g,
+                                          const T *__restrict__ ec, int Pc, T *__restrict__ psi_out, int N, int P,
+                                          int nu, T beta, bool want_norm, Correct64 cor, unsigned char *smem_raw) {
     T *sp = reinterpret_cast<T *>(smem_raw);
     int RX = halo_x(OP, nu), RY = halo_y(OP, nu);
     int LX = tile_lx(TX, OP, nu), LY = tile_ly(TY, nu), LP = tile_lp(LX);
     int LXc = tile_lxc(LX), LYc = tile_lxc(LY);
     T *sg = sp + LY * LP, *sc = sg + LY * LP;
-    int ox0 = 1 + blockIdx.x * TX, oy0 = 1 + blockIdx.y * TY;
+    int ox0 = 1 + bx * TX, oy0 = 1 + by * TY;
     int gx0 = ox0 - RX, gy0 = oy0 - RY;
     int Ic0 = gx0 >> 1, Jc0 = gy0 >> 1, Nc = N / 2;  // floor, also for negative gx0
     for (int y = threadIdx.y; y < LY; y += blockDim.y) {
@@ -329,12 +333,24 @@ __global__ void __launch_bounds__(512)
             } else {
                 psi_out[(size_t)gj * P + gi] = sp[c];
             }
-            if (partials) {
+            if (want_norm) {
                 double r = (double)(gs_local<T, OP>(sp, sg, c, LP) - sp[c]);
                 acc += r * r;
             }
         }
     }
+    return acc;  // this thread's share of the tile's sum of rho^2
+}
+
+template <typename T, int OP, int TX, int TY>
+__global__ void __launch_bounds__(512)
+    k_up(const T *__restrict__ psi_in, const T *__restrict__ g, const T *__restrict__ ec, int Pc,
+         T *__restrict__ psi_out, int N, int P, int nu, T beta, double *__restrict__ partials, Correct64 cor,
+         FinishArgs fin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    double acc = up_body<T, OP, TX, TY>(blockIdx.x, blockIdx.y, psi_in, g, ec, Pc, psi_out, N, P, nu, beta,
+                                        partials != nullptr, cor, smem_raw);
     if (partials) {
         acc = block_sum2d(acc, red);
         if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = acc;
@@ -378,11 +394,9 @@ __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
 }
 
 template <typename T, int OP>
-__global__ void __launch_bounds__(1024)
-    k_coarse(const T *__restrict__ g_in, int Pg, const T *__restrict__ psi_warm, T *__restrict__ psi_out, int Po,
-             int N0, int nl, int nu1, int nu2, int nuc, T beta, double *__restrict__ partial, FinishArgs fin) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+__device__ __forceinline__ double coarse_body(const T *__restrict__ g_in, int Pg, const T *__restrict__ psi_warm,
+                                              T *__restrict__ psi_out, int Po, int N0, int nl, int nu1, int nu2,
+                                              int nuc, T beta, bool want_norm, unsigned char *smem_raw) {
     T *base = reinterpret_cast<T *>(smem_raw);
     int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
     int tid = ty * bx + tx, nt = bx * by;
@@ -456,14 +470,25 @@ __global__ void __launch_bounds__(1024)
         for (int x = 1 + tx; x < N0; x += bx) {
             int q = y * L0 + x;
             psi_out[(size_t)y * Po + x] = base[q];
-            if (partial) {
+            if (want_norm) {
                 double r = (double)(gs_local<T, OP>(base, base + L0 * L0, q, L0) - base[q]);
                 acc += r * r;
             }
         }
+    return acc;
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(1024)
+    k_coarse(const T *__restrict__ g_in, int Pg, const T *__restrict__ psi_warm, T *__restrict__ psi_out, int Po,
+             int N0, int nl, int nu1, int nu2, int nuc, T beta, double *__restrict__ partial, FinishArgs fin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    double acc = coarse_body<T, OP>(g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial != nullptr,
+                                    smem_raw);
     if (partial) {
         acc = block_sum2d(acc, red);
-        if (tid == 0) partial[0] = acc;
+        if (threadIdx.x == 0 && threadIdx.y == 0) partial[0] = acc;
         if (fin.enabled) finish_if_last(partial, fin);
     }
 }
@@ -495,6 +520,44 @@ cudaError_t up_t(cudaStream_t s, const T *psi_in, const T *g, const T *ec, int P
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
     kern<<<grid, dim3(kTBX, kTBY), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms (mixed precision, FP32 correction hierarchy): one launch
+// covers the tiles of every cavity that still iterates; a cavity whose
+// Poisson loop has stopped leaves its blocks idle.
+template <int OP, int TX, int TY>
+__global__ void __launch_bounds__(512)
+    k_down_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int bx, by;
+    const BatchCav &cv = cav[batch_locate(r, bx, by)];
+    if (!cv.active) return;
+    down_body<float, OP, TX, TY>(bx, by, nullptr, 1, cv.g32[level], cv.eB[level], cv.N >> level, cv.P[level],
+                                 cv.g32[level + 1], cv.P[level + 1], nu, beta, smem_raw);
+}
+
+template <int OP, int TX, int TY>
+__global__ void __launch_bounds__(512)
+    k_up_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int bx, by;
+    const BatchCav &cv = cav[batch_locate(r, bx, by)];
+    if (!cv.active) return;
+    Correct64 cor{nullptr, 0, nullptr, 0};
+    if (level == 0) cor = Correct64{cv.psi64, cv.P[0], cv.psi32, cv.P[0]};
+    up_body<float, OP, TX, TY>(bx, by, cv.eB[level], cv.g32[level], cv.eA[level + 1], cv.P[level + 1], cv.eA[level],
+                               cv.N >> level, cv.P[level], nu, beta, false, cor, smem_raw);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, int nu2, int nuc, float beta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const BatchCav &cv = cav[blockIdx.x];
+    if (!cv.active) return;
+    int lc = cv.lc;
+    coarse_body<float, OP>(cv.g32[lc], cv.P[lc], nullptr, cv.eA[lc], cv.P[lc], cv.N >> lc, cv.nlev - lc, nu1, nu2, nuc,
+                           beta, false, smem_raw);
 }
 
 constexpr int kShapeTX[4] = {128, 64, 32, 16};
@@ -598,6 +661,71 @@ cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T
     return cudaGetLastError();
 }
 
+namespace {
+
+template <int OP, int TX, int TY>
+cudaError_t down_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
+                         float beta) {
+    k_down_batch<OP, TX, TY><<<nblocks, dim3(kTBX, kTBY), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
+                                                                                                 beta);
+    return cudaGetLastError();
+}
+
+template <int OP, int TX, int TY>
+cudaError_t up_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
+                       float beta) {
+    k_up_batch<OP, TX, TY><<<nblocks, dim3(kTBX, kTBY), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
+                                                                                               beta);
+    return cudaGetLastError();
+}
+
+template <int OP>
+cudaError_t down_batch_shape(cudaStream_t s, int shape, BatchCav *cav, const BatchRange *r, int level, int nb, int nu,
+                             float beta) {
+    switch (shape) {
+        case 0: return down_batch_t<OP, 128, 64>(s, cav, r, level, nb, nu, beta);
+        case 1: return down_batch_t<OP, 64, 64>(s, cav, r, level, nb, nu, beta);
+        case 2: return down_batch_t<OP, 32, 32>(s, cav, r, level, nb, nu, beta);
+        default: return down_batch_t<OP, 16, 16>(s, cav, r, level, nb, nu, beta);
+    }
+}
+
+template <int OP>
+cudaError_t up_batch_shape(cudaStream_t s, int shape, BatchCav *cav, const BatchRange *r, int level, int nb, int nu,
+                           float beta) {
+    switch (shape) {
+        case 0: return up_batch_t<OP, 128, 64>(s, cav, r, level, nb, nu, beta);
+        case 1: return up_batch_t<OP, 64, 64>(s, cav, r, level, nb, nu, beta);
+        case 2: return up_batch_t<OP, 32, 32>(s, cav, r, level, nb, nu, beta);
+        default: return up_batch_t<OP, 16, 16>(s, cav, r, level, nb, nu, beta);
+    }
+}
+
+}  // namespace
+
+template <>
+cudaError_t launch_down_batch<float>(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
+                                     int nblocks, int nu, float beta) {
+    return op == 1 ? down_batch_shape<1>(s, shape, cav, r, level, nblocks, nu, beta)
+                   : down_batch_shape<0>(s, shape, cav, r, level, nblocks, nu, beta);
+}
+
+template <>
+cudaError_t launch_up_batch<float>(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
+                                   int nblocks, int nu, float beta) {
+    return op == 1 ? up_batch_shape<1>(s, shape, cav, r, level, nblocks, nu, beta)
+                   : up_batch_shape<0>(s, shape, cav, r, level, nblocks, nu, beta);
+}
+
+cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count, int smem, int nu1, int nu2, int nuc,
+                                float beta) {
+    if (op == 1)
+        k_coarse_batch<1><<<count, dim3(32, 32), smem, s>>>(cav, nu1, nu2, nuc, beta);
+    else
+        k_coarse_batch<0><<<count, dim3(32, 32), smem, s>>>(cav, nu1, nu2, nuc, beta);
+    return cudaGetLastError();
+}
+
 // Raises every tile / coarse kernel's dynamic shared-memory limit once, before
 // any launch or graph capture.
 template <typename T>
@@ -616,9 +744,26 @@ static cudaError_t set_attrs_t() {
     return cudaSuccess;
 }
 
+template <int OP>
+static cudaError_t set_batch_attrs_t() {
+    const void *k[] = {(const void *)k_down_batch<OP, 128, 64>, (const void *)k_down_batch<OP, 64, 64>,
+                       (const void *)k_down_batch<OP, 32, 32>,  (const void *)k_down_batch<OP, 16, 16>,
+                       (const void *)k_up_batch<OP, 128, 64>,   (const void *)k_up_batch<OP, 64, 64>,
+                       (const void *)k_up_batch<OP, 32, 32>,    (const void *)k_up_batch<OP, 16, 16>,
+                       (const void *)k_coarse_batch<OP>};
+    for (const void *f : k) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t init_mg_kernel_attributes() {
     cudaError_t e = set_attrs_t<double>();
-    return e == cudaSuccess ? set_attrs_t<float>() : e;
+    if (e == cudaSuccess) e = set_attrs_t<float>();
+    if (e == cudaSuccess) e = set_batch_attrs_t<0>();
+    if (e == cudaSuccess) e = set_batch_attrs_t<1>();
+    return e;
 }
 
 #define LCX_MG_INSTANTIATE(T)                                                                                          \

@@ -163,7 +163,247 @@ __global__ void k_to32(const double *__restrict__ src, int P64, float *__restric
     dst[(size_t)j * P32 + i] = (float)src[(size_t)j * P64 + i];
 }
 
+// ---------------------------------------------------------------------------
+// Batched forms.  SSPRK(5,4) stage s reads stage buffer kIn[s] and writes
+// kOut[s] (0 = W0, 1 = Wa, 2 = Wb; ACC is W[3]); the coefficients are those of
+// the single-cavity step, with dt taken per cavity.
+__device__ __forceinline__ int stage_in(int s) { return s == 0 ? 0 : (s & 1 ? 1 : 2); }     // 0,1,2,1,2
+__device__ __forceinline__ int stage_out(int s) { return s == 4 ? 0 : (s & 1 ? 2 : 1); }   // 1,2,1,2,0
+
+__global__ void __launch_bounds__(kBX *kBY)
+    k_stage_batch(const BatchCav *cav, const BatchRange *r, int stage, StageCoef k, int advect) {
+    int bx, by;
+    const BatchCav &cv = cav[batch_locate(r, bx, by)];
+    int N = cv.N, P = cv.P[0];
+    int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
+    if (i >= N || j >= N) return;
+    size_t c = (size_t)j * P + i;
+    const float *in32 = cv.Ws[stage_in(stage)], *psi = cv.psi32;
+    const double *in64 = cv.W[stage_in(stage)], *W0 = cv.W[0];
+    double *acc = cv.W[3], *out64 = cv.W[stage_out(stage)];
+    float *out32 = cv.Ws[stage_out(stage)];
+    float inv2h = (float)(0.5 * N);
+    float nu_invh2 = (float)((double)N * (double)N / cv.Re);
+    float wP = in32[c], wE = in32[c + 1], wW = in32[c - 1], wN = in32[c + P], wS = in32[c - P];
+    float L = nu_invh2 * fmaf(-4.0f, wP, (wE + wW) + (wN + wS));
+    if (advect) {
+        float u = (psi[c + P] - psi[c - P]) * inv2h;
+        float v = -(psi[c + 1] - psi[c - 1]) * inv2h;
+        float tx = u * ((wE - wW) * inv2h);
+        float ty = v * ((wN - wS) * inv2h);
+        L = (L - tx) - ty;
+    }
+    double Ld = (double)L, wPd = in64[c];
+    double bdt = k.bdt * cv.dt, o;
+    if (k.mode == 3) {
+        o = fma(bdt, Ld, fma(k.a1, wPd, acc[c]));
+    } else {
+        o = fma(bdt, Ld, fma(k.a1, wPd, k.a0 * W0[c]));
+        if (k.mode == 1) acc[c] = k.acc_in * wPd;
+        else if (k.mode == 2) acc[c] = fma(k.acc_L * cv.dt, Ld, fma(k.acc_in, wPd, acc[c]));
+    }
+    out64[c] = o;
+    out32[c] = (float)o;
+}
+
+// Poisson right-hand side (as k_assemble_rhs) of every cavity's new stage
+// vorticity, per-block partial sums of g^2, and the start of each cavity's
+// solve (all cavities iterate again).
+template <int OP>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_assemble_batch(BatchCav *cav, const BatchRange *r, int stage, double *__restrict__ gpart) {
+    __shared__ double sh[32];
+    int bx, by;
+    int ci = batch_locate(r, bx, by);
+    BatchCav &cv = cav[ci];
+    if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) cv.active = 1;
+    int N = cv.N, P = cv.P[0];
+    const double *w = cv.W[stage_out(stage)];
+    double h2 = (1.0 / N) * (1.0 / N);
+    int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
+    double v = 0.0;
+    if (i < N && j < N) {
+        size_t c = (size_t)j * P + i;
+        double val;
+        if (OP == 1)
+            val = h2 * fma(8.0, w[c], (w[c + 1] + w[c - 1]) + (w[c + P] + w[c - P])) * (1.0 / 40.0);
+        else
+            val = 0.25 * h2 * w[c];
+        cv.g64[c] = val;
+        v = val * val;
+    }
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) gpart[blockIdx.x] = v;
+}
+
+// FP64 residual of every active cavity rounded to FP32 (as k_residual64_to32)
+// with per-block partial sums of rho^2.  With fin.enabled, the last block of
+// each cavity applies that cavity's stopping rule (same rule and summation
+// order as the single-cavity finisher), and the last cavity to finish sets
+// the loop condition: go on while any cavity iterates.
+template <int OP>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_residual_batch(BatchCav *cav, const BatchRange *r, double *__restrict__ rpart, const double *__restrict__ gpart,
+                     BatchFinish fin) {
+    __shared__ double sh[32];
+    __shared__ unsigned int s_last;
+    int bx, by;
+    int ci = batch_locate(r, bx, by);
+    BatchCav &cv = cav[ci];
+    int N = cv.N, P = cv.P[0];
+    int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
+    double v = 0.0;
+    if (cv.active && i < N && j < N) {
+        const double *psi = cv.psi64, *g = cv.g64;
+        size_t c = (size_t)j * P + i;
+        double n4 = (psi[c + 1] + psi[c - 1]) + (psi[c + P] + psi[c - P]);
+        double gs;
+        if (OP == 1) {
+            double d4 = (psi[c + P + 1] + psi[c + P - 1]) + (psi[c - P + 1] + psi[c - P - 1]);
+            gs = fma(0.2, n4, fma(0.05, d4, g[c]));
+        } else {
+            gs = fma(0.25, n4, g[c]);
+        }
+        double rho = gs - psi[c];
+        cv.g32[0][c] = (float)rho;
+        v = rho * rho;
+    }
+    v = block_sum(v, sh);
+    int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    if (tid == 0) rpart[blockIdx.x] = v;
+    if (!fin.enabled) return;
+    int b0 = r->start[ci], nb = r->start[ci + 1] - b0;
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(&cv.arrive, 1u) == (unsigned)nb - 1 ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (cv.active) {
+        double sr = 0.0, sg = 0.0;
+        for (int k = tid; k < nb; k += nt) sr += __ldcg(rpart + b0 + k);
+        for (int k = tid; k < nb; k += nt) sg += __ldcg(gpart + b0 + k);
+        sr = block_sum(sr, sh);
+        sg = block_sum(sg, sh);
+        if (tid == 0) {
+            int cyc = cv.cycles + 1;
+            double rn = sqrt(sr), gn = sqrt(sg);
+            bool finite = isfinite(rn) && isfinite(gn);
+            bool more = false;
+            if (!finite) {
+                cv.status |= kStatusNonFinite;
+            } else if (rn <= fin.tol * gn) {
+            } else if (cyc >= fin.max_cycles) {
+                cv.status |= kStatusNoConv;
+            } else {
+                more = true;
+            }
+            if (more) {
+                cv.cycles = cyc;
+            } else {
+                cv.cycles = 0;
+                cv.active = 0;
+                cv.last_cycles = cyc;
+                cv.last_rel = gn > 0.0 ? rn / gn : (rn > 0.0 ? INFINITY : 0.0);
+                cv.log[cv.nsolves % kLogN] = cyc;
+                cv.nsolves += 1;
+            }
+        }
+    }
+    if (tid != 0) return;
+    cv.arrive = 0;
+    __threadfence();
+    if (atomicAdd(&fin.bs->cav_arrive, 1u) != (unsigned)r->count - 1) return;
+    __threadfence();
+    fin.bs->cav_arrive = 0;
+    unsigned int any = 0;
+    for (int c = 0; c < r->count; ++c) any |= (unsigned)((volatile BatchCav *)cav)[c].active;
+    if (fin.h)
+        cudaGraphSetConditional(fin.h, any ? 1u : 0u);
+    else
+        fin.bs->more = (int)any;
+}
+
+// Thom's wall vorticity for every cavity (blockIdx.y = cavity), uniform lid U.
+__global__ void k_thom_batch(const BatchCav *cav, double U) {
+    const BatchCav &cv = cav[blockIdx.y];
+    int N = cv.N, P = cv.P[0];
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = N - 1;
+    double m2h2 = -2.0 * (double)N * (double)N;
+    const double *psi = cv.psi64;
+    int i, j;
+    double val;
+    if (t < n) {
+        i = t + 1;
+        j = 0;
+        val = m2h2 * psi[(size_t)P + i];
+    } else if (t < 2 * n) {
+        i = t - n + 1;
+        j = N;
+        val = m2h2 * psi[(size_t)(N - 1) * P + i] - 2.0 * U * N;
+    } else if (t < 3 * n) {
+        j = t - 2 * n + 1;
+        i = 0;
+        val = m2h2 * psi[(size_t)j * P + 1];
+    } else if (t < 4 * n) {
+        j = t - 3 * n + 1;
+        i = N;
+        val = m2h2 * psi[(size_t)j * P + N - 1];
+    } else if (t < 4 * n + 4) {
+        int k = t - 4 * n;
+        i = k & 1 ? N : 0;
+        j = k & 2 ? N : 0;
+        val = 0.0;
+    } else {
+        return;
+    }
+    for (int b = 0; b < 3; ++b) {
+        cv.W[b][(size_t)j * P + i] = val;
+        cv.Ws[b][(size_t)j * P + i] = (float)val;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
+                               int advect) {
+    // SSPRK(5,4) stage coefficients, Eqs. (9)-(13): bdt and acc_L are scaled by each cavity's dt in the kernel
+    static const StageCoef kc[5] = {
+        {1.0, 0.0, 0.391752226571890, 0.0, 0.0, 0},
+        {0.444370493651235, 0.555629506348765, 0.368410593050371, 0.0, 0.0, 0},
+        {0.620101851488403, 0.379898148511597, 0.251891774271694, 0.517231671970585, 0.0, 1},
+        {0.178079954393132, 0.821920045606868, 0.544974750228521, 0.096059710526147, 0.063692468666290, 2},
+        {0.0, 0.386708617503269, 0.226007483236906, 0.0, 0.0, 3}};
+    k_stage_batch<<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
+                                  double *gpart) {
+    if (op == 1)
+        k_assemble_batch<1><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, gpart);
+    else
+        k_assemble_batch<0><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, gpart);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks,
+                                  double *rpart, const double *gpart, BatchFinish fin) {
+    if (op == 1)
+        k_residual_batch<1><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
+    else
+        k_residual_batch<0><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U) {
+    // N <= 8192: 4 (N - 1) + 4 <= 32768 wall nodes
+    k_thom_batch<<<dim3(32768 / 256, count), 256, 0, s>>>(cav, U);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
                                    float *r32, int P32, double *partials, FinishArgs fin) {

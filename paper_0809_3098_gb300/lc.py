@@ -75,6 +75,19 @@ def lib() -> ctypes.CDLL:
         "lc_launch_stats": ([vp, _dp], ci),
         "lc_bench_kernel": ([vp, ci, ci, _dp], ci),
         "lc_monitor_noalloc": ([ci, vp, vp, vp, vp, sz, cd, vp, vp], ci),
+        "lc_batch_create": ([ci, ctypes.POINTER(ci), _dp, _dp, cd, ci], vp),
+        "lc_batch_destroy": ([vp], None),
+        "lc_batch_set_option": ([vp, ctypes.c_char_p, cd], ci),
+        "lc_batch_set_stream": ([vp, vp], ci),
+        "lc_batch_workspace_bytes": ([ci, ctypes.POINTER(ci), ci], sz),
+        "lc_batch_bind_workspace": ([vp, vp, sz], ci),
+        "lc_batch_step": ([vp, ci], ci),
+        "lc_batch_get": ([vp, ci, ci, _dp, sz], ci),
+        "lc_batch_set_state": ([vp, ci, _dp, _dp], ci),
+        "lc_batch_cycle_log": ([vp, ci, ctypes.POINTER(ci), sz, ctypes.POINTER(sz)], ci),
+        "lc_batch_synchronize": ([vp], ci),
+        "lc_batch_info": ([vp, ci, _dp], ci),
+        "lc_batch_autotune": ([vp, ci, ctypes.POINTER(ci), ci], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -294,6 +307,110 @@ class Cavity:
     def close(self) -> None:
         if getattr(self, "_h", None):
             lc_destroy(self._h)
+            self._h = None
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many cavities advanced together (``lc_batch_*``; mixed precision).
+
+    ``Ns`` / ``Res`` give each cavity's size and Reynolds number; ``dts``
+    (optional) its time step (<= 0: the rule).  Workspace and stream as
+    :class:`Cavity`.
+    """
+
+    def __init__(self, Ns, Res, dts=None, tol: float = 1e-10, *, workspace: str = "torch", stream=None,
+                 **options):
+        n = len(Ns)
+        self.Ns = [int(x) for x in Ns]
+        self._ws = None
+        Na = (ctypes.c_int * n)(*self.Ns)
+        Ra = np.ascontiguousarray(Res, dtype=np.float64)
+        Da = np.ascontiguousarray(dts if dts is not None else np.zeros(n), dtype=np.float64)
+        self._h = lib().lc_batch_create(n, Na, _p(Ra), _p(Da), tol, LC_PREC_MIXED)
+        if not self._h:
+            raise LCError(LC_ERR_ARG, "lc_batch_create")
+        try:
+            for key in ("op", "coarse_max"):
+                if key in options:
+                    self.set_option(key, options.pop(key))
+            for k, v in options.items():
+                self.set_option(k, v)
+            if workspace == "torch":
+                import torch
+
+                nbytes = lib().lc_batch_workspace_bytes(n, Na, LC_PREC_MIXED)
+                self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+                _check(lib().lc_batch_bind_workspace(self._h, self._ws.data_ptr(), nbytes), "lc_batch_bind_workspace")
+                s = stream if stream is not None else torch.cuda.current_stream()
+                _check(lib().lc_batch_set_stream(self._h, s.cuda_stream), "lc_batch_set_stream")
+            elif stream is not None:
+                _check(lib().lc_batch_set_stream(self._h, stream.cuda_stream), "lc_batch_set_stream")
+        except Exception:
+            self.close()
+            raise
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    @property
+    def count(self) -> int:
+        return len(self.Ns)
+
+    def set_option(self, key: str, value: float) -> None:
+        _check(lib().lc_batch_set_option(self._h, key.encode(), float(value)), f"lc_batch_set_option({key})")
+
+    def step(self, n: int = 1) -> None:
+        _check(lib().lc_batch_step(self._h, n), "lc_batch_step")
+
+    def synchronize(self) -> None:
+        _check(lib().lc_batch_synchronize(self._h), "lc_batch_synchronize")
+
+    def _get(self, c: int, field: int) -> np.ndarray:
+        N = self.Ns[c]
+        out = np.empty((N + 1, N + 1))
+        _check(lib().lc_batch_get(self._h, c, field, _p(out), out.size), "lc_batch_get")
+        return out
+
+    def psi(self, c: int) -> np.ndarray:
+        return self._get(c, 0)
+
+    def omega(self, c: int) -> np.ndarray:
+        return self._get(c, 1)
+
+    def set_state(self, c: int, psi, omega) -> None:
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        omega = np.ascontiguousarray(omega, dtype=np.float64)
+        _check(lib().lc_batch_set_state(self._h, c, _p(psi), _p(omega)), "lc_batch_set_state")
+
+    def cycle_log(self, c: int) -> np.ndarray:
+        out = np.zeros(65536, dtype=np.int32)
+        n = ctypes.c_size_t(0)
+        _check(lib().lc_batch_cycle_log(self._h, c, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), out.size,
+                                        ctypes.byref(n)), "lc_batch_cycle_log")
+        return out[: n.value].copy()
+
+    def info(self, c: int) -> dict:
+        out = np.zeros(8)
+        _check(lib().lc_batch_info(self._h, c, _p(out)), "lc_batch_info")
+        return dict(N=int(out[0]), Re=out[1], dt=out[2], levels=int(out[3]), coarse_level=int(out[4]),
+                    steps=int(out[5]), tile_shape0=int(out[6]), workspace_bytes=int(out[7]))
+
+    def autotune(self, reps: int = 5) -> list:
+        shapes = (ctypes.c_int * 16)()
+        _check(lib().lc_batch_autotune(self._h, reps, shapes, 16), "lc_batch_autotune")
+        return [s for s in shapes if s >= 0]
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().lc_batch_destroy(self._h)
             self._h = None
         self._ws = None
 
