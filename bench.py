@@ -8,7 +8,14 @@ the default workload: 1024x1024 intervals, Re = 10000, lid u = 1, dt =
 fourth-order Poisson operator, starting from rest (synthetic, deterministic).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload fp64-1024|fp64-128]
+                  [--workload fp64-1024|fp64-128|fp64-4096] [--precision fp64|mixed]
+                  [--eager] [--no-cpu-baseline] [--no-e2e] [--no-variants]
+
+--precision mixed runs the same workload with FP32 V-cycles and FP32
+L(omega) stencils inside FP64 residual, refinement, Thom and stage
+accumulation.  --eager launches the step's kernels one by one (the V-cycle
+loop driven from the host) so that a profiler can attribute them; it is
+slower and only for profiling.
 
 Our arm times K steps with CUDA events on the context's stream, flushing L2
 (a 256 MiB write) between timed steps, and prints one JSON line with the
@@ -53,7 +60,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="fp64-1024")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--eager", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -167,11 +178,186 @@ def run_reference(args, wl: Workload):
     return 0
 
 
-def config_of(wl: Workload, gpus: int) -> dict:
-    return {"workload": wl.name, "N": wl.N, "Re": wl.Re, "dt": wl.dt, "tol": wl.tol, "op": wl.op,
-            "precision": wl.precision, "start": "rest (psi = omega = 0)",
+def config_of(wl: Workload, gpus: int, precision: str = "fp64") -> dict:
+    name = wl.name if precision == "fp64" else wl.name.replace("-fp64", "-mixed")
+    return {"workload": name, "N": wl.N, "Re": wl.Re, "dt": wl.dt, "tol": wl.tol, "op": wl.op,
+            "precision": precision, "start": "rest (psi = omega = 0)",
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": "replicas" if gpus > 1 else "single"}
+
+
+FP32_FMA_PER_CLK_PER_SM = 128
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The slowest rank's time: all-reduce MAX over the process group (any backend)."""
+    import torch
+
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most max_ms."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+# Kernels lc_bench_kernel can time, and how many times each runs per step
+# (c = V-cycles in the step's five solves).
+KERNELS = {
+    "fp64": [("k_smooth_colour<double,compact> (fine level, one colour phase)", lambda c, nu: 4 * 2 * nu * c),
+             ("k_rhs_stage (fused L(omega) + stage combination)", lambda c, nu: 5),
+             ("k_residual_restrict<double,compact> (fine level)", lambda c, nu: c)],
+    "mixed": [("k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)", lambda c, nu: c),
+              ("k_rhs_stage_mixed (FP32 L(omega) + FP64 stage combination)", lambda c, nu: 5),
+              ("k_residual64_to32<compact> (FP64 residual, rounded to FP32)", lambda c, nu: c + 5),
+              ("k_up<float,compact> (fine level: FP32 post-smoothing + FP64 psi += e)", lambda c, nu: c)],
+}
+
+
+def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> dict:
+    """Times each fine-level kernel of the step (lc_bench_kernel, CUDA events on
+    the context stream, the same arguments as in the step) and reports the one
+    with the largest share of the step against whichever peak binds it."""
+    hbm, max_mhz, src = peaks()
+    mhz = clocks.get("sm_mhz") or max_mhz
+    p64 = fp64_peak_tflops(mhz)
+    p32 = SMS * FP32_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
+    rows = []
+    for kid, (name, count) in enumerate(KERNELS[precision]):
+        ms, nbytes, f64, f32 = lc.lc_bench_kernel(cav.handle, kid, 100)
+        share_ms = ms * count(cycles_per_step, 2)
+        fr = {"hbm": nbytes / (ms * 1e-3) / 1e9 / hbm, "alu64": f64 / (ms * 1e-3) / 1e12 / p64,
+              "alu32": f32 / (ms * 1e-3) / 1e12 / p32}
+        rows.append((share_ms, kid, name, ms, nbytes, f64, f32, fr))
+    share_ms, kid, name, ms, nbytes, f64, f32, fr = max(rows)
+    bound = max(fr, key=fr.get)
+    if bound == "hbm":
+        roof = {"bound": "hbm", "achieved": nbytes / (ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json), of {src}"}
+    else:
+        fl, pk = (f64, p64) if bound == "alu64" else (f32, p32)
+        roof = {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                "peak_source": (f"derived: {SMS} SMs x "
+                                f"{FP64_FMA_PER_CLK_PER_SM if bound == 'alu64' else FP32_FMA_PER_CLK_PER_SM} "
+                                f"{'FP64' if bound == 'alu64' else 'FP32'} FMA/clk x 2 flop x {mhz:.0f} MHz "
+                                f"(median SM clock under load)")}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["kernel"] = name
+    roof["kernel_ms"] = ms
+    roof["launches_per_step"] = KERNELS[precision][kid][1](cycles_per_step, 2)
+    roof["algorithmic_bytes"] = nbytes
+    roof["fp64_flops"] = f64
+    roof["fp32_flops"] = f32
+    roof["fractions"] = fr
+    roof["all_kernels_ms"] = {r[2]: r[3] for r in sorted(rows, key=lambda r: r[1])}
+    return roof
+
+
+def timed_run(lc, torch, dist, wl: Workload, precision: str, steps: int, warmup: int, eager: bool, world: int,
+              sample_clocks: int | None):
+    """W warm-up steps, then K steps each bracketed by CUDA events on the
+    context's stream, with an L2 flush between them."""
+    opts = {"op": lc.LC_OP_COMPACT, "precision": lc.LC_PREC_MIXED if precision == "mixed" else lc.LC_PREC_FP64}
+    if eager:
+        opts["graph"] = 0
+    cav = lc.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **opts)
+    stream = torch.cuda.current_stream()
+    cav.step(warmup)
+    cav.synchronize()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    n_before = len(cav.cycle_log())
+    sampler = None
+    if sample_clocks is not None:
+        sampler = ClockSampler(sample_clocks)
+        sampler.start()
+        time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(steps):
+        flush.fill_(k & 0xFF)  # evicts the previous step's working set from L2
+        ev[k][0].record(stream)
+        cav.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else {}
+    cav.synchronize()
+    total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist if world > 1 else None, "cuda")
+    cycles = cav.cycle_log()[n_before:]
+    per_step_fixed, per_cycle = lc.lc_launch_stats(cav.handle)
+    return {
+        "cav": cav, "total_ms": total_ms, "wall_ms": wall * 1e3, "clocks": clocks,
+        "cycles": cycles, "launches": int(steps * per_step_fixed + per_cycle * int(cycles.sum())),
+        "value": job_rate(world, wl.interior_nodes * 5 * steps, total_ms),
+    }
+
+
+def mixed_bytes_per_node(cycles_per_step: float) -> float:
+    """Algorithmic DRAM bytes per interior node of one mixed-precision step
+    (each array element read or written once per kernel):
+    L(omega) + stage combination over the five stages 28+36+44+52+36 = 196 B;
+    Poisson right-hand side 5 x 16 B; the first FP64 residual of each solve
+    5 x 20 B; per refinement cycle: fine-level FP32 pre-smoothing tile 9 B
+    (r32 in, e32 out, coarse g out), post-smoothing tile + psi64 += e 29 B
+    (e32, r32, coarse e in; psi64 in and out, psi32 out), FP64 residual 20 B
+    (psi64, g64 in; r32 out), and the coarser levels' tiles, 22 B per coarse
+    node summed over levels (22/4 + 22/16 + ...)."""
+    per_cycle = 9.0 + 29.0 + 20.0 + 22.0 / 3.0
+    return 196.0 + 80.0 + 100.0 + cycles_per_step * per_cycle
+
+
+def run_batch(lc, torch, args, world: int) -> dict:
+    import numpy as np
+
+    from paper_0809_3098_gb300.workloads import batch_cavities
+
+    cav = batch_cavities(32, seed=0)
+    Ns, Res = [n for n, _ in cav], [r for _, r in cav]
+    b = lc.Batch(Ns, Res)
+    b.step(1)
+    b.synchronize()
+    shapes = b.autotune(reps=3)
+    b.step(max(args.warmup - 1, 0))
+    b.synchronize()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    n_before = [len(b.cycle_log(c)) for c in range(b.count)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        b.step(1)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    b.synchronize()
+    total_ms = sum(a.elapsed_time(c) for a, c in ev)
+    nodes = [(n - 1) ** 2 for n in Ns]
+    cyc = [b.cycle_log(c)[n_before[c]:] for c in range(b.count)]
+    per_step_cycles = [x.sum() / args.steps for x in cyc]
+    nbytes = sum(n * mixed_bytes_per_node(c) for n, c in zip(nodes, per_step_cycles)) * args.steps
+    hbm, _, src = peaks()
+    gbs = nbytes / (total_ms * 1e-3) / 1e9
+    b.close()
+    return {
+        "value": world * sum(nodes) * 5 * args.steps / (total_ms * 1e-3), "unit": UNIT,
+        "ms_per_step": total_ms / args.steps, "cavities": len(Ns), "interior_nodes": sum(nodes),
+        "N": Ns, "Re": [round(r, 1) for r in Res], "vcycles_per_solve": float(np.mean(np.concatenate(cyc))) / 1.0,
+        "tile_shapes_autotuned": shapes,
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "scope": "whole step: algorithmic bytes of every kernel / step time",
+                     "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"},
+        "l2": "flushed between timed steps (256 MiB write); the batch's arrays (~1 GB) exceed L2",
+    }
 
 
 def run_ours(args, wl: Workload):
@@ -188,98 +374,64 @@ def run_ours(args, wl: Workload):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    cav = lc.Cavity(wl.N, wl.Re, wl.dt, wl.tol, op=lc.LC_OP_COMPACT)
-    stream = torch.cuda.current_stream()
-    cav.step(args.warmup)
-    cav.synchronize()
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    n_before = len(cav.cycle_log())
-
-    sampler = ClockSampler(local)
-    sampler.start()
-    time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)  # evicts the previous step's working set from L2
-        ev[k][0].record(stream)
-        cav.step(1)
-        ev[k][1].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - w0
-    if world > 1:
-        dist.barrier()
-    clocks = sampler.stop()
-    cav.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    cycles = cav.cycle_log()[n_before:]
-    per_step_fixed, per_cycle = lc.lc_launch_stats(cav.handle)
-    launches = int(args.steps * per_step_fixed + per_cycle * int(cycles.sum()))
-
-    updates = wl.interior_nodes * 5 * args.steps
-    value = world * updates / (total_ms / 1e3)
+    r = timed_run(lc, torch, dist, wl, args.precision, args.steps, args.warmup, args.eager, world, local)
+    cav = r["cav"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_of(wl, world),
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
+        "data": "synthetic", "config": config_of(wl, world, args.precision),
     }
-    line["config"]["wall_ms_timed_region"] = wall * 1e3
-    line["config"]["vcycles_per_solve"] = float(cycles.mean()) if len(cycles) else None
-    line["gpu_launches"] = launches
-    line["clocks"] = clocks
+    line["config"]["wall_ms_timed_region"] = r["wall_ms"]
+    line["config"]["vcycles_per_solve"] = float(r["cycles"].mean()) if len(r["cycles"]) else None
+    if args.eager:
+        line["config"]["launch"] = "eager (profiling)"
+    line["gpu_launches"] = r["launches"]
+    line["clocks"] = r["clocks"]
 
-    # --- roofline of the dominant kernel: the fine-level smoother colour phase
-    hbm, max_mhz, src = peaks()
-    reps = 200
-    k = lc.lc_bench_kernel(cav.handle, 0, reps)
-    ms, nbytes, f64 = k[0], k[1], k[2]
-    mhz_load = clocks.get("sm_mhz") or max_mhz
-    p64 = fp64_peak_tflops(mhz_load)
-    ach_tf = f64 / (ms * 1e-3) / 1e12
-    ach_gbs = nbytes / (ms * 1e-3) / 1e9
-    alu_frac, hbm_frac = ach_tf / p64, ach_gbs / hbm
-    if alu_frac >= hbm_frac:
-        roof = {"bound": "alu", "achieved": ach_tf, "peak": p64, "unit": "TFLOP/s", "frac": alu_frac}
-        roof["peak_source"] = (f"derived: {SMS} SMs x {FP64_FMA_PER_CLK_PER_SM} FP64 FMA/clk x 2 flop x "
-                               f"{mhz_load:.0f} MHz (median SM clock under load)")
-    else:
-        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": hbm_frac,
-                "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"}
-    roof["traffic"] = None
-    roof["kernel"] = "k_smooth_colour<double,compact> (fine level, one colour phase)"
-    roof["kernel_ms"] = ms
-    roof["algorithmic_bytes"] = nbytes
-    roof["fp64_flops"] = f64
-    roof["hbm_frac"] = hbm_frac
-    roof["alu_frac"] = alu_frac
-    line["roofline"] = roof
+    cyc_per_step = float(r["cycles"].sum()) / max(args.steps, 1)
+    state = (cav.psi(), cav.omega())
+    line["roofline"] = roofline(lc, cav, args.precision, cyc_per_step, r["clocks"])
 
     # --- end to end through the C ABI with host buffers (pinned)
-    n = (wl.N + 1) ** 2
-    hp = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.N + 1, wl.N + 1)
-    hw = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.N + 1, wl.N + 1)
-    hp[:] = cav.psi()
-    hw[:] = cav.omega()
-    e2e_steps = max(3, min(args.steps, 10))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        cav.set_state(hp, hw)
-        cav.step(1)
-        lc.lc_get_psi(cav.handle, hp)
-        lc._check(lc.lc_get_omega(cav.handle, hw), "lc_get_omega")
-    e2e_s = time.perf_counter() - t0
-    line["e2e"] = {"value": world * wl.interior_nodes * 5 * e2e_steps / e2e_s, "unit": UNIT,
-                   "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n,
-                   "steps": e2e_steps, "api": "lc_set_state + lc_step(1) + lc_get_psi + lc_get_omega"}
+    if not args.no_e2e:
+        n = (wl.N + 1) ** 2
+        hp = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.N + 1, wl.N + 1)
+        hw = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy().reshape(wl.N + 1, wl.N + 1)
+        hp[:], hw[:] = state
+        e2e_steps = max(3, min(args.steps, 10))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            cav.set_state(hp, hw)
+            cav.step(1)
+            lc._check(lc.lc_get_psi(cav.handle, hp), "lc_get_psi")
+            lc._check(lc.lc_get_omega(cav.handle, hw), "lc_get_omega")
+        e2e_s = time.perf_counter() - t0
+        line["e2e"] = {"value": world * wl.interior_nodes * 5 * e2e_steps / e2e_s, "unit": UNIT,
+                       "h2d_bytes_per_step": 2 * 8 * n, "d2h_bytes_per_step": 2 * 8 * n,
+                       "steps": e2e_steps, "api": "lc_set_state + lc_step(1) + lc_get_psi + lc_get_omega"}
+    cav.close()
+
+    # --- the mixed-precision form of the same workload, and its error against this FP64 run
+    if not args.no_variants and args.precision == "fp64" and not args.eager:
+        m = timed_run(lc, torch, dist, wl, "mixed", args.steps, args.warmup, False, world, None)
+        mc = m["cav"]
+        ep = float(np.abs(mc.psi() - state[0]).max() / np.abs(state[0]).max())
+        ew = float(np.abs(mc.omega() - state[1]).max() / np.abs(state[1]).max())
+        mcyc = float(m["cycles"].sum()) / max(args.steps, 1)
+        line["variants"] = {"mixed": {
+            "value": m["value"], "unit": UNIT, "ms_per_step": m["total_ms"] / args.steps,
+            "speedup_vs_fp64": m["value"] / r["value"], "vcycles_per_solve": float(m["cycles"].mean()),
+            "gpu_launches": m["launches"],
+            "rel_err_vs_fp64": {"psi": ep, "omega": ew, "after_steps": args.warmup + args.steps},
+            "roofline": roofline(lc, mc, "mixed", mcyc, r["clocks"]),
+        }}
+        mc.close()
+
+    # --- the batched form: 32 cavities of uneven N and Re in one graph launch per step
+    if not args.no_variants and args.precision == "fp64" and not args.eager:
+        line["variants"]["batch32_mixed"] = run_batch(lc, torch, args, world)
 
     # --- CPU oracle on this host (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -289,7 +441,6 @@ def run_ours(args, wl: Workload):
                                           f"({el:.1f} s), plain C FP64, one thread"}
     if rank == 0:
         print(json.dumps(line))
-    cav.close()
     if world > 1:
         dist.destroy_process_group()
     return 0

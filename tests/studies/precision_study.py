@@ -1,0 +1,92 @@
+"""Precision study: the mixed-precision step against the FP64 step on the
+lid-driven cavity, 1024x1024 intervals, Re in {5000, 10000, 20000, 30000},
+dt by the rule 0.25 min(h, Re h^2 / 4), Poisson tol 1e-10, from rest.
+
+Both runs use the CUDA library; the FP64 path is itself held to the plain
+FP64 oracle at 1e-10 by the parity tests.  Reported per Re: the relative
+max-norm error max|x - x_fp64| / max|x_fp64| of psi, omega, the vertical
+centreline u(y) at x = 1/2 and the horizontal centreline v(x) at y = 1/2
+(central differences of psi, Eq. (22); wall values by the boundary
+conditions), and both paths' step times.  The mixed runs go through the
+batched engine (all Re in one launch per step), which gives the bits of
+single-cavity mixed runs.
+
+    python -m tests.studies.precision_study --steps 20000 [--N 1024] > precision.json
+"""
+import argparse
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+
+def centrelines(psi: np.ndarray):
+    N = psi.shape[0] - 1
+    h = 1.0 / N
+    m = N // 2
+    u = np.zeros(N + 1)
+    u[1:N] = (psi[2:, m] - psi[:-2, m]) / (2 * h)  # u(y) at x = 1/2, psi[j, i]
+    u[N] = 1.0
+    v = np.zeros(N + 1)
+    v[1:N] = -(psi[m, 2:] - psi[m, :-2]) / (2 * h)  # v(x) at y = 1/2
+    return u, v
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--Re", type=float, nargs="*", default=[5000.0, 10000.0, 20000.0, 30000.0])
+    args = ap.parse_args()
+    import torch
+
+    from paper_0809_3098_gb300 import lc
+
+    torch.cuda.set_device(0)
+    out = {"N": args.N, "steps": args.steps, "tol": 1e-10, "results": []}
+    t0 = time.perf_counter()
+    batch = lc.Batch([args.N] * len(args.Re), args.Re)
+    batch.step(args.steps)
+    batch.synchronize()
+    t_mixed = time.perf_counter() - t0
+    for c, Re in enumerate(args.Re):
+        t1 = time.perf_counter()
+        ref = lc.Cavity(args.N, Re, monitor=1)
+        monitors = []
+        done = 0
+        while done < args.steps:  # the steady-state monitors every 1000 steps
+            n = min(1000, args.steps - done)
+            ref.step(n)
+            done += n
+            m = ref.monitor()
+            monitors.append({"step": done, "max_domega_dt": m[0], "RES_psi": m[1], "RES_omega": m[2]})
+        ref.synchronize()
+        t_fp64 = time.perf_counter() - t1
+        p64, w64 = ref.psi(), ref.omega()
+        pm, wm = batch.psi(c), batch.omega(c)
+        u64, v64 = centrelines(p64)
+        um, vm = centrelines(pm)
+        row = {"Re": Re, "dt": ref.params["dt"], "t_end": ref.params["dt"] * args.steps,
+               "rel_err": {"psi": rel(pm, p64), "omega": rel(wm, w64), "u_centre": rel(um, u64),
+                           "v_centre": rel(vm, v64)},
+               "psi_min": float(p64.min()), "fp64_seconds": t_fp64, "fp64_monitors": monitors,
+               "vcycles_per_solve": {"fp64": float(ref.cycle_log().mean()),
+                                     "mixed": float(batch.cycle_log(c).mean())}}
+        out["results"].append(row)
+        ref.close()
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    out["mixed_batch_seconds"] = t_mixed
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()
