@@ -62,6 +62,9 @@ def lib():
         L.or_apply_operator.argtypes = [ci, ci, _dp, _dp]
         L.or_residual.argtypes = [ci, ci, _dp, _dp, _dp]
         L.or_smooth.argtypes = [ci, ci, _dp, _dp, cd, ci]
+        L.or_sor_lex.argtypes = [ci, ci, _dp, _dp, cd, ci]
+        L.or_sor_solve.argtypes = [ci, ci, _dp, _dp, cd, ci, ci, cd, _dp]
+        L.or_sor_solve.restype = ci
         L.or_restrict.argtypes = [ci, _dp, _dp]
         L.or_prolong_add.argtypes = [ci, _dp, _dp]
         L.or_poisson_solve.argtypes = [ci, ci, _dp, _dp, cd, ci, ci, ci, cd, _dp]
@@ -153,6 +156,25 @@ def smooth(N: int, op: int, psi, f, beta: float = 1.0, nsweeps: int = 1) -> np.n
     psi = _f64(psi).copy()
     lib().or_smooth(N, op, _p(psi), _p(_f64(f)), beta, nsweeps)
     return psi
+
+
+def sor_lex(N: int, op: int, psi, f, beta: float = 1.0, nsweeps: int = 1) -> np.ndarray:
+    """SOR sweeps of Eq. (15) in the order of its superscripts (i outer, j inner)."""
+    psi = _f64(psi).copy()
+    lib().or_sor_lex(N, op, _p(psi), _p(_f64(f)), beta, nsweeps)
+    return psi
+
+
+def sor_solve(N: int, op: int, f, psi0=None, tol: float = 1e-10, max_checks: int = 1000,
+              sweeps_per_check: int = 16, beta: float = 1.0):
+    """Lexicographic SOR solve of L_h psi = f (reading R13): passes of
+    sweeps_per_check sweeps until the stopping test of R7 holds.  Returns
+    (psi, passes, rel); passes is negative (ERR_NOCONV) if max_checks ran out."""
+    psi = _field(N) if psi0 is None else _f64(psi0).copy()
+    rel = ctypes.c_double(0.0)
+    n = lib().or_sor_solve(N, op, _p(_f64(f)), _p(psi), tol, max_checks, sweeps_per_check, beta,
+                           ctypes.byref(rel))
+    return psi, n, rel.value
 
 
 def restrict(Nf: int, r) -> np.ndarray:

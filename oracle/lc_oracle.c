@@ -47,6 +47,11 @@
  *       colours (i mod 2, j mod 2) for the compact operator).
  *   R8  psi(omega^{n+1}) is solved at the end of each step, so a step makes
  *       five solves and the next step's first stage reuses it.
+ *   R12 multigrid halves a level while its interval count is even and >= 4;
+ *       the coarsest level (2, 3, 5 or 7 intervals) gets nuc smoothing sweeps.
+ *   R13 the alternative solver "SOR" is Eq. (15) on its own, swept in the
+ *       order its n / n+1 superscripts fix (i outer, j inner), with the
+ *       stopping test of R7 after every sor_sweeps sweeps.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -54,6 +59,8 @@
 
 #define OR_OP_5PT 0
 #define OR_OP_COMPACT 1
+#define OR_SOLVER_MG 0
+#define OR_SOLVER_SOR 1
 
 #define OR_OK 0
 #define OR_ERR_ARG -1
@@ -208,6 +215,27 @@ void or_smooth(int N, int op, double *psi, const double *f, double beta, int nsw
                 }
 }
 
+/* nsweeps sweeps of the SOR update, Eq. (15), in the order its superscripts
+ * fix.  At node (i, j) the equation takes psi at (i-1, j-1), (i-1, j),
+ * (i-1, j+1) and (i, j-1) from the current sweep (n+1) and psi at (i+1, j-1),
+ * (i+1, j), (i+1, j+1) and (i, j+1) from the previous one (n): i is the outer
+ * (slow) loop and j the inner (fast) loop, and updating in place in that
+ * order is exactly the method.  Same node formula as or_smooth. */
+void or_sor_lex(int N, int op, double *psi, const double *f, double beta, int nsweeps) {
+    double h = 1.0 / N, b = 1.0 / (h * h), c = 1.0 / (h * h), a = b + c;
+    for (int s = 0; s < nsweeps; ++s)
+        for (int i = 1; i < N; ++i)
+            for (int j = 1; j < N; ++j) {
+                double A = term_A(N, b, c, psi, i, j);
+                double B = -f[AT(N, i, j)];
+                double old = psi[AT(N, i, j)];
+                if (op == OR_OP_COMPACT)
+                    psi[AT(N, i, j)] = 3.0 / 5.0 * beta / a * (A + B + term_C(N, a, psi, i, j)) + (1.0 - beta) * old;
+                else
+                    psi[AT(N, i, j)] = 0.5 * beta / a * (A + B) + (1.0 - beta) * old;
+            }
+}
+
 /* Full-weighting restriction of a fine interior field (Nf intervals) onto the
  * coarse grid (Nf/2 intervals): weights 1/16 [1 2 1; 2 4 2; 1 2 1]. */
 void or_restrict(int Nf, const double *rf, double *fc) {
@@ -254,8 +282,9 @@ static double interior_norm2(int N, const double *x) {
 
 /* ------------------------------------------------------------------------ */
 /* Geometric multigrid.  Level 0 is the fine grid; a level is halved while its
- * interval count is even and at least 4, so the coarsest level has 2 or 3
- * intervals (N must be 2^k or 3*2^k).  Coarse operators are the same
+ * interval count is even and at least 4, so the coarsest level has 2, 3, 5 or
+ * 7 intervals (N must be 2^k, 3*2^k, 5*2^k or 7*2^k), where nuc sweeps of the
+ * smoother stand in for a solve.  Coarse operators are the same
  * discretisation re-applied with the coarse h. */
 #define OR_MAX_LEVELS 16
 
@@ -264,8 +293,10 @@ typedef struct {
     double *psi, *f, *r;
 } or_level;
 
+/* solver OR_SOLVER_MG: one "cycle" is a V(nu1, nu2) cycle; OR_SOLVER_SOR:
+ * one "cycle" is sor_sweeps lexicographic SOR sweeps on the fine grid. */
 typedef struct {
-    int op, nlev, nu1, nu2, nuc;
+    int op, nlev, nu1, nu2, nuc, solver, sor_sweeps;
     double beta;
     or_level lev[OR_MAX_LEVELS];
 } or_mg;
@@ -276,7 +307,7 @@ static int mg_level_count(int N) {
         N /= 2;
         ++n;
     }
-    return (N == 2 || N == 3) ? n : -1;
+    return (N == 2 || N == 3 || N == 5 || N == 7) ? n : -1;
 }
 
 static int mg_init(or_mg *mg, int N, int op) {
@@ -287,6 +318,8 @@ static int mg_init(or_mg *mg, int N, int op) {
     mg->nu1 = 2;
     mg->nu2 = 2;
     mg->nuc = 16;
+    mg->solver = OR_SOLVER_MG;
+    mg->sor_sweeps = 16;
     mg->beta = 1.0;
     for (int l = 0; l < nlev; ++l) {
         int n = N >> l;
@@ -327,7 +360,8 @@ static void vcycle(or_mg *mg, int l) {
 
 /* Solve L_h psi = f (reading R7).  psi holds the warm start on entry and the
  * solution on return (walls untouched, i.e. zero).  Returns the number of
- * V-cycles; *rel receives ||f - L_h psi|| / ||f|| (0 if both are zero). */
+ * cycles (V-cycles, or passes of sor_sweeps SOR sweeps); *rel receives
+ * ||f - L_h psi|| / ||f|| (0 if both are zero). */
 static int mg_solve(or_mg *mg, double *psi, double *f, double tol, int max_cycles, double *rel, int *status) {
     or_level *F = &mg->lev[0];
     F->psi = psi;
@@ -336,7 +370,10 @@ static int mg_solve(or_mg *mg, double *psi, double *f, double tol, int max_cycle
     int cycles = 0;
     double rnorm;
     for (;;) {
-        vcycle(mg, 0);
+        if (mg->solver == OR_SOLVER_SOR)
+            or_sor_lex(F->N, mg->op, psi, f, mg->beta, mg->sor_sweeps);
+        else
+            vcycle(mg, 0);
         ++cycles;
         or_residual(F->N, mg->op, psi, f, F->r);
         rnorm = interior_norm2(F->N, F->r);
@@ -370,6 +407,27 @@ int or_poisson_solve(int N, int op, const double *f, double *psi, double tol, in
     int status = OR_OK;
     double rel = 0.0;
     int cycles = mg_solve(&mg, psi, fc, tol, max_cycles, &rel, &status);
+    if (rel_out) *rel_out = rel;
+    free(fc);
+    mg_free(&mg);
+    return status == OR_OK ? cycles : status;
+}
+
+/* Stand-alone lexicographic SOR solve for the pins: passes of sweeps_per_check
+ * sweeps, each followed by the stopping test of mg_solve. */
+int or_sor_solve(int N, int op, const double *f, double *psi, double tol, int max_checks, int sweeps_per_check,
+                 double beta, double *rel_out) {
+    or_mg mg;
+    if (mg_init(&mg, N, op) != OR_OK) return OR_ERR_ARG;
+    mg.solver = OR_SOLVER_SOR;
+    mg.sor_sweeps = sweeps_per_check;
+    mg.beta = beta;
+    size_t m = (size_t)(N + 1) * (N + 1);
+    double *fc = malloc(sizeof(double) * m);
+    memcpy(fc, f, sizeof(double) * m);
+    int status = OR_OK;
+    double rel = 0.0;
+    int cycles = mg_solve(&mg, psi, fc, tol, max_checks, &rel, &status);
     if (rel_out) *rel_out = rel;
     free(fc);
     mg_free(&mg);
@@ -529,7 +587,8 @@ void or_destroy(void *p) {
 }
 
 /* Options: "U", "profile", "advect", "max_cycles", "nu1", "nu2", "nuc",
- * "beta".  Changing the lid re-applies Thom to the current psi. */
+ * "beta", "solver" (0 multigrid, 1 lexicographic SOR), "sor_sweeps".
+ * Changing the lid re-applies Thom to the current psi. */
 int or_set_option(void *p, const char *key, double value) {
     or_cavity *cv = (or_cavity *)p;
     if (!cv || !key) return OR_ERR_ARG;
@@ -543,6 +602,8 @@ int or_set_option(void *p, const char *key, double value) {
     else if (!strcmp(key, "nu2")) cv->mg.nu2 = (int)value;
     else if (!strcmp(key, "nuc")) cv->mg.nuc = (int)value;
     else if (!strcmp(key, "beta")) cv->mg.beta = value;
+    else if (!strcmp(key, "solver")) cv->mg.solver = (int)value;
+    else if (!strcmp(key, "sor_sweeps")) cv->mg.sor_sweeps = (int)value;
     else return OR_ERR_ARG;
     return OR_OK;
 }

@@ -138,7 +138,7 @@ def test_set_state_reapplies_thom_and_continues():
 
 def test_rejects_bad_arguments():
     with pytest.raises(ValueError):
-        oracle.Cavity(20, 100.0, 1e-3)       # 20 = 4 * 5 does not coarsen to 2 or 3
+        oracle.Cavity(44, 100.0, 1e-3)       # 44 = 4 * 11 does not coarsen to 2, 3, 5 or 7
     with pytest.raises(ValueError):
         oracle.Cavity(16, -1.0, 1e-3)
     with pytest.raises(ValueError):

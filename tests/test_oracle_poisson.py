@@ -58,7 +58,7 @@ def test_compact_rhs_eigenvector(N):
     assert np.array_equal(interior(f5), -interior(S))
 
 
-@pytest.mark.parametrize("N", [16, 48, 128])
+@pytest.mark.parametrize("N", [16, 48, 80, 112, 128])
 @pytest.mark.parametrize("op", OPS)
 def test_solve_returns_discrete_eigenvector(N, op):
     X, Y = grid(N)
@@ -119,7 +119,7 @@ def random_rhs(N, seed):
     return f
 
 
-@pytest.mark.parametrize("N", [16, 24, 96])
+@pytest.mark.parametrize("N", [16, 24, 40, 56, 96])
 @pytest.mark.parametrize("op", OPS)
 def test_solve_matches_direct_dst(N, op):
     f = random_rhs(N, seed=N + 7 * op)
@@ -198,10 +198,11 @@ def test_restriction_of_constant_and_walls():
     assert np.allclose(fc[1:-1, 1:-1], 2.5, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("N", [128, 224, 320])
 @pytest.mark.parametrize("op", OPS)
-def test_multigrid_contraction(op):
-    """A V(2,2) cycle contracts the residual by at least 5x per cycle."""
-    N = 128
+def test_multigrid_contraction(op, N):
+    """A V(2,2) cycle contracts the residual by at least 5x per cycle, also
+    when the coarsest grid has 7 (224 = 7 * 32) or 5 (320 = 5 * 64) intervals."""
     f = random_rhs(N, seed=1)
     psi = np.zeros_like(f)
     prev = np.linalg.norm(f)
@@ -219,6 +220,6 @@ def test_zero_rhs_gives_zero_in_one_cycle():
 
 
 def test_rejects_unsupported_sizes():
-    f = np.zeros((21, 21))
-    psi, cycles, rel = oracle.poisson_solve(20, OP_5PT, f)
+    f = np.zeros((37, 37))
+    psi, cycles, rel = oracle.poisson_solve(36, OP_5PT, f)   # 36 = 4 * 9
     assert cycles == oracle.ERR_ARG
