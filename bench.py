@@ -306,13 +306,14 @@ def mixed_bytes_per_node(cycles_per_step: float) -> float:
     (each array element read or written once per kernel):
     L(omega) + stage combination over the five stages 28+36+44+52+36 = 196 B;
     Poisson right-hand side 5 x 16 B; the first FP64 residual of each solve
-    5 x 20 B; per refinement cycle: fine-level FP32 pre-smoothing tile 9 B
-    (r32 in, e32 out, coarse g out), post-smoothing tile + psi64 += e 29 B
-    (e32, r32, coarse e in; psi64 in and out, psi32 out), FP64 residual 20 B
-    (psi64, g64 in; r32 out), and the coarser levels' tiles, 22 B per coarse
-    node summed over levels (22/4 + 22/16 + ...)."""
-    per_cycle = 9.0 + 29.0 + 20.0 + 22.0 / 3.0
-    return 196.0 + 80.0 + 100.0 + cycles_per_step * per_cycle
+    5 x 20 B; the FP32 shadow of psi after each solve 5 x 12 B; per
+    refinement cycle: fine-level FP32 pre-smoothing tile 9 B (r32 in, e32
+    out, coarse g out), post-smoothing tile + psi64 += e 25 B (e32, r32,
+    coarse e in; psi64 in and out), FP64 residual 20 B (psi64, g64 in; r32
+    out), and the coarser levels' tiles, 22 B per coarse node summed over
+    levels (22/4 + 22/16 + ...)."""
+    per_cycle = 9.0 + 25.0 + 20.0 + 22.0 / 3.0
+    return 196.0 + 80.0 + 100.0 + 60.0 + cycles_per_step * per_cycle
 
 
 def run_batch(lc, torch, args, world: int) -> dict:
@@ -325,6 +326,7 @@ def run_batch(lc, torch, args, world: int) -> dict:
     b = lc.Batch(Ns, Res)
     b.step(1)
     b.synchronize()
+    schedule = b.autotune_schedule(steps=2)
     shapes = b.autotune(reps=3)
     b.step(max(args.warmup - 1, 0))
     b.synchronize()
@@ -352,12 +354,28 @@ def run_batch(lc, torch, args, world: int) -> dict:
         "value": world * sum(nodes) * 5 * args.steps / (total_ms * 1e-3), "unit": UNIT,
         "ms_per_step": total_ms / args.steps, "cavities": len(Ns), "interior_nodes": sum(nodes),
         "N": Ns, "Re": [round(r, 1) for r in Res], "vcycles_per_solve": float(np.mean(np.concatenate(cyc))) / 1.0,
-        "tile_shapes_autotuned": shapes,
+        "tile_shapes_autotuned": shapes, "schedule_autotuned": {"nu1": schedule[0], "nu2": schedule[1]},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                      "scope": "whole step: algorithmic bytes of every kernel / step time",
                      "peak_source": f"{src} copy bandwidth (MEASURED_PEAKS.json)"},
         "l2": "flushed between timed steps (256 MiB write); the batch's arrays (~1 GB) exceed L2",
     }
+
+
+def run_sor(lc, torch, wl: Workload) -> dict:
+    """Throughput of the lexicographic SOR kernel (Eq. (15) in its own order,
+    16 sweeps per launch) on the workload's grid: node updates per second."""
+    cav = lc.Cavity(wl.N, wl.Re, sor_sweeps=16, beta=1.5)
+    cav.step(1)
+    cav.synchronize()
+    reps = 3
+    r = lc.lc_bench_kernel(cav.handle, 3, reps)
+    cav.close()
+    ms = r[0]
+    upd = 16 * (wl.N - 1) ** 2
+    return {"value": upd / (ms * 1e-3), "unit": "node updates/s", "ms_per_16_sweeps": ms,
+            "fp64_tflops": r[2] / (ms * 1e-3) / 1e12,
+            "note": "one thread block (the sweep order is sequential beyond a wavefront); not a step rate"}
 
 
 def run_ours(args, wl: Workload):
@@ -432,6 +450,10 @@ def run_ours(args, wl: Workload):
     # --- the batched form: 32 cavities of uneven N and Re in one graph launch per step
     if not args.no_variants and args.precision == "fp64" and not args.eager:
         line["variants"]["batch32_mixed"] = run_batch(lc, torch, args, world)
+
+    # --- the paper's own solver: lexicographic SOR sweeps (wavefront kernel, one block)
+    if not args.no_variants and args.precision == "fp64" and not args.eager:
+        line["variants"]["sor_lex_sweeps"] = run_sor(lc, torch, wl)
 
     # --- CPU oracle on this host (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -25,7 +25,8 @@
  * have (N+1) x (N+1) nodes.  Every host array exchanged through this ABI is
  * FP64, row-major, index j*(N+1) + i, with i the x index (0 = left wall,
  * N = right wall) and j the y index (0 = bottom wall, N = lid).  N must be
- * 2^k or 3*2^k with 8 <= N <= 8192 (multigrid halves N down to 2 or 3).
+ * 2^k, 3*2^k, 5*2^k or 7*2^k with 8 <= N <= 8192 (multigrid halves N down
+ * to 2, 3, 5 or 7 intervals).
  *
  * Time step.  One step is one SSPRK(5,4) step: five Runge-Kutta stages and
  * five Poisson solves (psi is re-solved at the end of the step so that the
@@ -111,7 +112,15 @@ const char *lc_last_error(void);
  *   "nu1","nu2"   pre/post smoothing sweeps per level (2, 2), 1..16
  *   "nuc"         sweeps on the coarsest grid (16), 1..256
  *   "beta"        relaxation of the SOR update, Eq. (15) (1.0), 0 < beta < 2
- *   "max_cycles"  V-cycle cap per solve (100); hitting it raises LC_ERR_NOCONV
+ *   "max_cycles"  cycle cap per solve (100); hitting it raises LC_ERR_NOCONV
+ *   "solver"      0 (default) multigrid V-cycles; 1 the paper's SOR iteration
+ *                 alone: Eq. (15) swept lexicographically in the order its
+ *                 n / n+1 superscripts fix (i outer, j inner), a "cycle" being
+ *                 sor_sweeps sweeps followed by the stopping test.  FP64 only.
+ *   "sor_sweeps"  sweeps per SOR cycle (16), 1..4096
+ *   "rhs64"       mixed precision only: 1 evaluates L(omega) (Eq. (8)) in FP64
+ *                 from the FP64 psi and omega instead of their FP32 shadows
+ *                 (default 0); the multigrid corrections stay FP32
  *   "U"           lid speed (1.0); re-applies Thom to the current state
  *   "profile"     0 uniform lid (default), 1 regularised lid 16x^2(1-x)^2 U
  *   "advect"      1 (default), 0 drops the transport terms of Eq. (8)
@@ -127,7 +136,7 @@ const char *lc_last_error(void);
  *                 in a single thread block (default -1: 32 for FP64, 64 for
  *                 mixed precision), 2..256.
  *   "tile_shape"  -1 (default) picks each level's tile shape; 0..3 forces
- *                 128x64, 64x64, 32x32 or 16x16 owned nodes per tile.
+ *                 110x54, 110x22, 46x22 or 16x16 owned nodes per tile.
  *   "graph"       1 (default) replays each step as one CUDA graph whose
  *                 V-cycle loops are device-side while-nodes; 0 launches the
  *                 same kernels one by one and drives the V-cycle loop from the
@@ -197,7 +206,8 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * on the context stream.  FP64 precision: kernel 0 = fine-level smoother
  * colour phase (the colours taken in turn), 1 = fused L(omega) + stage
  * combination (stage 2), 2 = fine-level residual + full-weighting
- * restriction.  Mixed precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
+ * restriction, 3 = one lexicographic SOR pass of sor_sweeps sweeps.  Mixed
+ * precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
  * residual, restriction), 1 = FP32 L(omega) + FP64 stage combination (stage
  * 2), 2 = FP64 residual rounded to FP32, 3 = fine-level FP32 tile kernel
  * (prolongation, post-smoothing, FP64 psi += e).  out[0] = mean ms per
@@ -218,7 +228,8 @@ int lc_bench_kernel(lc_ctx *ctx, int kernel, int reps, double out[4]);
  * a single-cavity context with the same options. */
 typedef struct lc_batch lc_batch;
 
-/* count (1..256) cavities; N[c] must be 2^k or 3*2^k in 128..8192; Re[c] > 0;
+/* count (1..256) cavities; N[c] must be 2^k, 3*2^k, 5*2^k or 7*2^k in 128..8192;
+ * Re[c] > 0;
  * dt may be NULL or hold dt[c] <= 0 to apply dt = 0.25 min(h, Re h^2 / 4);
  * tol as lc_create; precision must be LC_PREC_MIXED.  All cavities start at
  * rest (as lc_create).  NULL on error (lc_last_error). */
@@ -226,7 +237,8 @@ lc_batch *lc_batch_create(int count, const int *N, const double *Re, const doubl
 void lc_batch_destroy(lc_batch *b);
 
 /* Options as lc_set_option: "op", "coarse_max" (8..64) [before first use],
- * "nu1", "nu2" (1..4), "nuc", "beta", "max_cycles", "U", "advect", "graph". */
+ * "nu1", "nu2" (1..4), "nuc", "beta", "max_cycles", "U", "advect", "rhs64",
+ * "graph". */
 int lc_batch_set_option(lc_batch *b, const char *key, double value);
 int lc_batch_set_stream(lc_batch *b, void *cuda_stream);
 size_t lc_batch_workspace_bytes(int count, const int *N, int precision);
@@ -253,12 +265,25 @@ int lc_batch_synchronize(lc_batch *b);
 int lc_batch_info(lc_batch *b, int cavity, double out[8]);
 
 /* Autotuner: for every tile level, times `reps` launches of the batch's
- * pre- and post-smoothing tile kernels in each tile shape (128x64, 64x64,
- * 32x32, 16x16 owned nodes; those that fit in shared memory) on the current
+ * pre- and post-smoothing tile kernels in each tile shape (110x54, 110x22,
+ * 46x22, 16x16 owned nodes; those that fit in shared memory) on the current
  * state, keeps the fastest, and writes the chosen shape per level to
  * shapes_out[0..max_levels) (-1 past the last tile level).  The tile shape
  * does not change any result (bit-identical); the state is restored. */
 int lc_batch_autotune(lc_batch *b, int reps, int *shapes_out, int max_levels);
+
+/* Smoothing-schedule autotuner: for each schedule (nu1, nu2) in (1,1), (2,1),
+ * (1,2), (2,2), (3,1), (3,2) it runs one untimed and then `steps` >= 1 timed
+ * steps of the whole batch from the current state (tile shapes chosen by the
+ * cost model), restores the state (the workspace is snapshotted into a
+ * temporary device buffer of lc_batch_workspace_bytes), and keeps the
+ * schedule with the least time per step among those whose solves all
+ * converged.  Every schedule solves to the same tolerance, so results change
+ * only within it; the cycle counts change with the schedule.  Writes the
+ * chosen (nu1, nu2) to nu_out[0..1] and sets them as options; tile shapes
+ * are reset to the cost model's (call lc_batch_autotune afterwards to tune
+ * them for the chosen schedule).  LC_ERR_NOCONV if no schedule converged. */
+int lc_batch_autotune_schedule(lc_batch *b, int steps, int nu_out[2]);
 
 /* Largest N accepted by lc_monitor_noalloc: the size of its fixed scratch. */
 #define LC_NOALLOC_MAX_N 8192

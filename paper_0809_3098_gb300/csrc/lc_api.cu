@@ -66,7 +66,7 @@ int level_count(int N) {
         N /= 2;
         ++n;
     }
-    return (N == 2 || N == 3) ? n : -1;
+    return (N == 2 || N == 3 || N == 5 || N == 7) ? n : -1;
 }
 
 bool valid_N(int N) { return N >= 8 && N <= 8192 && level_count(N) >= 2; }
@@ -129,7 +129,7 @@ bool make_layout(int N, int precision, Layout &L) {
     L.snap_psi = take(n0 * sizeof(double));
     L.snap_w = take(n0 * sizeof(double));
     L.nrpart_grid = residual_norm_blocks(N);
-    L.nrpart = L.nrpart_grid > tiles_of(N, 3) ? L.nrpart_grid : tiles_of(N, 3);  // 16x16 tiles: the most partials
+    L.nrpart = L.nrpart_grid > tiles_of(N, 3) ? L.nrpart_grid : tiles_of(N, 3);  // the smallest tiles: the most partials
     L.ngpart = assemble_blocks(N);
     L.nmpart = monitor_blocks(N);
     L.rpart = take(L.nrpart * sizeof(double));
@@ -151,6 +151,8 @@ struct lc_ctx {
     int nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
     int use_graph = 1;
     double beta = 1.0, U = 1.0;
+    int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR
+    int rhs64 = 0;                                      // mixed precision: L(omega) in FP64
     int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
     int tile_force = -1;                                // >= 0: one tile shape on every level
 
@@ -327,14 +329,13 @@ int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h
     LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc], L.nlev - lc,
                                  c->nu1, c->nu2, c->nuc, beta, nullptr, kNoFinish));
     ++k;
-    float *psi32 = c->at<float>(L.psi32);
     if (lc == 0) {
-        LC_CUDA(launch_correct64(s, c->eA(0), L.Pl[0], c->psi(0), L.Pl[0], psi32, L.Pl[0], c->N));
+        LC_CUDA(launch_correct64(s, c->eA(0), L.Pl[0], c->psi(0), L.Pl[0], nullptr, L.Pl[0], c->N));
         ++k;
     }
     for (int l = lc - 1; l >= 0; --l, ++k) {
         Correct64 cor{nullptr, 0, nullptr, 0};
-        if (l == 0) cor = Correct64{c->psi(0), L.Pl[0], psi32, L.Pl[0]};
+        if (l == 0) cor = Correct64{c->psi(0), L.Pl[0], nullptr, L.Pl[0]};
         LC_CUDA(launch_up<float>(s, tile_shape(c, l), c->op, c->eB(l), c->g32(l), c->eA(l + 1), L.Pl[l + 1], c->eA(l),
                                  L.Nl[l], L.Pl[l], c->nu2, beta, nullptr, cor, kNoFinish));
     }
@@ -350,6 +351,13 @@ int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h
 int enqueue_cycle_body(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) {
     const Layout &L = c->lay;
     if (c->mixed()) return enqueue_vcycle_mixed(c, s, h);
+    if (c->solver == 1) {  // one pass of sor_sweeps lexicographic sweeps, then the stopping test
+        LC_CUDA(launch_sor_lex(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->sor_sweeps, c->beta));
+        LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<double>(L.rpart),
+                                             finish_args(c, L.nrpart_grid, h)));
+        c->kernels_per_cycle = 2;
+        return LC_OK;
+    }
     bool norm_done = false;
     int rc = enqueue_vcycle(c, s, &norm_done, h);
     if (rc) return rc;
@@ -382,6 +390,15 @@ void stage_plan(const lc_ctx *c, StagePlan st[5]) {
     st[4] = {Wb, W0, Wbs, W0s, StageCoef{0.0, A54, B54 * dt, 0.0, 0.0, 3}};
 }
 
+// Mixed precision: the FP32 shadow of psi, read only by the next stage's
+// L(omega), is refreshed once after each solve.
+int enqueue_psi32(lc_ctx *c, cudaStream_t s) {
+    if (!c->mixed() || c->rhs64) return LC_OK;
+    const Layout &L = c->lay;
+    LC_CUDA(launch_to32(s, c->psi(0), L.Pl[0], c->at<float>(L.psi32), L.Pl[0], c->N));
+    return LC_OK;
+}
+
 int enqueue_thom(lc_ctx *c, cudaStream_t s) {
     const Layout &L = c->lay;
     if (c->mixed()) {
@@ -399,7 +416,13 @@ int enqueue_thom(lc_ctx *c, cudaStream_t s) {
 int enqueue_stage_head(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
     const Layout &L = c->lay;
     int N = c->N, P = L.Pl[0];
-    if (c->mixed()) {
+    if (c->mixed() && c->rhs64) {  // FP64 L(omega) from psi64; FP32 multigrid corrections
+        LC_CUDA(launch_rhs_stage(s, c->psi(0), st.in64, c->at<double>(L.W0), c->at<double>(L.ACC), st.out64, N, P,
+                                 c->Re, c->advect, st.k));
+        LC_CUDA(launch_assemble_rhs(s, c->op, st.out64, c->g(0), N, P, c->at<double>(L.gpart)));
+        LC_CUDA(launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
+                                       c->at<double>(L.rpart), kNoFinish));
+    } else if (c->mixed()) {
         LC_CUDA(launch_rhs_stage_mixed(s, c->at<float>(L.psi32), P, st.in32, st.in64, c->at<double>(L.W0),
                                        c->at<double>(L.ACC), st.out64, st.out32, N, P, P, c->Re, c->advect, st.k));
         LC_CUDA(launch_assemble_rhs(s, c->op, st.out64, c->g(0), N, P, c->at<double>(L.gpart)));
@@ -440,7 +463,8 @@ int capture_stage(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
     cudaError_t e2 = cudaStreamEndCapture(c->cap2, &tmp);
     if (rc != LC_OK) return rc;
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture(body)");
-    return enqueue_thom(c, s);
+    rc = enqueue_psi32(c, s);
+    return rc ? rc : enqueue_thom(c, s);
 }
 
 // Eager mode: the same kernels launched one by one, the V-cycle loop driven
@@ -461,7 +485,8 @@ int eager_step(lc_ctx *c) {
             LC_CUDA(cudaStreamSynchronize(s));
             if (!more) break;
         }
-        rc = enqueue_thom(c, s);
+        rc = enqueue_psi32(c, s);
+        if (rc == LC_OK) rc = enqueue_thom(c, s);
         if (rc) return rc;
     }
     return LC_OK;
@@ -489,8 +514,8 @@ int build_graph(lc_ctx *c) {
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     c->graph = g;
-    // per stage: L + combination, Poisson right-hand side, (mixed: first residual), Thom
-    c->kernels_per_step = 5 * (c->mixed() ? 4 : 3);
+    // per stage: L + combination, Poisson right-hand side, (mixed: first residual, psi shadow), Thom
+    c->kernels_per_step = 5 * (c->mixed() ? (c->rhs64 ? 4 : 5) : 3);
     LC_CUDA(cudaGraphInstantiate(&c->exec, c->graph, 0));
     c->graph_dirty = false;
     return LC_OK;
@@ -500,6 +525,7 @@ int ensure_init(lc_ctx *c) {
     if (c->initialized) return LC_OK;
     LC_CUDA(cudaGetDevice(&c->device));
     LC_CUDA(init_mg_kernel_attributes());
+    LC_CUDA(init_sor_kernel_attributes());
     if (!c->ws) {
         void *p = nullptr;
         LC_CUDA(cudaMalloc(&p, c->lay.total));
@@ -550,7 +576,7 @@ extern "C" {
 
 lc_ctx *lc_create(int N, double Re, double dt, double tol) {
     if (!valid_N(N)) {
-        fail(LC_ERR_ARG, "N must be 2^k or 3*2^k with 8 <= N <= 8192");
+        fail(LC_ERR_ARG, "N must be 2^k, 3*2^k, 5*2^k or 7*2^k with 8 <= N <= 8192");
         return nullptr;
     }
     if (!(Re > 0.0) || !std::isfinite(Re) || !(tol > 0.0) || !std::isfinite(dt)) {
@@ -636,6 +662,7 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "precision") {
         if (c->initialized) return fail(LC_ERR_ARG, "precision must be set before first use");
         if (!integral || (iv != LC_PREC_FP64 && iv != LC_PREC_MIXED)) return fail(LC_ERR_ARG, "precision must be 0 or 1");
+        if (iv == LC_PREC_MIXED && c->solver == 1) return fail(LC_ERR_ARG, "the SOR solver runs in FP64 precision only");
         c->precision = iv;
         make_layout(c->N, c->precision, c->lay);
     } else if (k == "nu1" || k == "nu2") {
@@ -647,6 +674,16 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "beta") {
         if (!(v > 0.0 && v < 2.0)) return fail(LC_ERR_ARG, "beta must be in (0, 2)");
         c->beta = v;
+    } else if (k == "solver") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "solver must be 0 (multigrid) or 1 (SOR)");
+        if (iv == 1 && c->mixed()) return fail(LC_ERR_ARG, "the SOR solver runs in FP64 precision only");
+        c->solver = iv;
+    } else if (k == "rhs64") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "rhs64 must be 0 or 1");
+        c->rhs64 = iv;
+    } else if (k == "sor_sweeps") {
+        if (!integral || iv < 1 || iv > 4096) return fail(LC_ERR_ARG, "sor_sweeps must be 1..4096");
+        c->sor_sweeps = iv;
     } else if (k == "max_cycles") {
         if (!integral || iv < 1) return fail(LC_ERR_ARG, "max_cycles must be >= 1");
         c->max_cycles = iv;
@@ -829,7 +866,7 @@ int lc_launch_stats(lc_ctx *c, double out[2]) {
 
 int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
     LC_CHECK_CTX(c);
-    int nk = c->mixed() ? 4 : 3;
+    int nk = 4;
     if (!out || reps < 1 || kernel < 0 || kernel >= nk) return fail(LC_ERR_ARG, "bad kernel id, reps or output");
     int rc = ensure_init(c);
     if (rc) return rc;
@@ -849,9 +886,11 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 case 1:
                     return launch_rhs_stage(s, c->psi(0), c->at<double>(L.Wa), c->at<double>(L.W0),
                                             c->at<double>(L.ACC), c->at<double>(L.Wb), N, P, c->Re, c->advect, k2);
-                default:
+                case 2:
                     return launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), N, P, c->g(1), c->psi(1),
                                                             L.Pl[1]);
+                default:
+                    return launch_sor_lex(s, c->op, c->psi(0), c->g(0), N, P, c->sor_sweeps, c->beta);
             }
         }
         switch (kernel) {
@@ -866,7 +905,7 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 return launch_residual64_to32(s, c->op, c->psi(0), c->g(0), N, P, c->at<float>(L.r32), P,
                                               c->at<double>(L.rpart), kNoFinish);
             default: {
-                Correct64 cor{c->psi(0), P, c->at<float>(L.psi32), P};
+                Correct64 cor{c->psi(0), P, nullptr, P};
                 return launch_up<float>(s, tile_shape(c, 0), c->op, c->eB(0), c->g32(0), c->eA(1), L.Pl[1], c->eA(0), N,
                                         P, c->nu2, (float)c->beta, nullptr, cor, kNoFinish);
             }
@@ -900,9 +939,13 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 out[1] = 32.0 * n_int;
                 out[2] = (c->advect ? 27.0 : 13.0) * n_int;
                 break;
-            default:  // read psi, g; write the coarse g and zero the coarse psi
+            case 2:  // read psi, g; write the coarse g and zero the coarse psi
                 out[1] = 16.0 * n_int + 16.0 * n_c;
                 out[2] = res_flops * n_int + 8.0 * n_c;
+                break;
+            default:  // sor_sweeps sweeps; the grid is read and written once per launch
+                out[1] = 24.0 * n_int;
+                out[2] = c->sor_sweeps * (sw_flops + (c->beta != 1.0 ? 3.0 : 0.0)) * n_int;
         }
     } else {
         switch (kernel) {
@@ -919,8 +962,8 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 out[1] = 20.0 * n_int;
                 out[2] = (res_flops + 1.0) * n_int;
                 break;
-            default:  // read e32, r32, coarse e, psi64; write psi64 and psi32
-                out[1] = 28.0 * n_int + 4.0 * n_c;
+            default:  // read e32, r32, coarse e, psi64; write psi64
+                out[1] = 24.0 * n_int + 4.0 * n_c;
                 out[2] = 1.0 * n_int;
                 out[3] = (c->nu2 * sw_flops + 3.0) * n_int;
         }

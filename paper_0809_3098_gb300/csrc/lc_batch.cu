@@ -53,7 +53,7 @@ int nlevels(int N) {
         N /= 2;
         ++n;
     }
-    return (N == 2 || N == 3) ? n : -1;
+    return (N == 2 || N == 3 || N == 5 || N == 7) ? n : -1;
 }
 
 constexpr int kSBX = 32, kSBY = 8;  // stage-kernel block
@@ -73,7 +73,7 @@ struct lc_batch {
     std::vector<double> Re, dt;
     double tol = 1e-10, beta = 1.0, U = 1.0;
     int op = LC_OP_COMPACT, nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
-    int use_graph = 1;
+    int use_graph = 1, rhs64 = 0;
     int Lmax = 0;
     std::vector<int> shape;  // tile shape per level (< Lmax)
 
@@ -247,13 +247,12 @@ void fill_tables(lc_batch *b) {
     for (int l = 0; l < b->Lmax; ++l) {
         BatchRange &r = b->hr[1 + l];
         int sh = shape_of(b, l);
-        static const int TX[4] = {128, 64, 32, 16}, TY[4] = {64, 64, 32, 16};
         r.count = C;
         int s = 0;
         for (int c = 0; c < C; ++c) {
             r.start[c] = s;
             int n = b->N[c] >> l;
-            int gx = (n - 1 + TX[sh] - 1) / TX[sh], gy = (n - 1 + TY[sh] - 1) / TY[sh];
+            int gx = (n - 1 + tile_tx(sh) - 1) / tile_tx(sh), gy = (n - 1 + tile_ty(sh) - 1) / tile_ty(sh);
             r.gx[c] = gx;
             if (l < b->lc[c]) s += gx * gy;
         }
@@ -315,7 +314,7 @@ int enqueue_cycle(lc_batch *b, cudaStream_t s, cudaGraphConditionalHandle h) {
 }
 
 int enqueue_head(lc_batch *b, cudaStream_t s, int stage) {
-    LB_CUDA(launch_stage_batch(s, b->dcav(), b->drange(0), b->rblocks[0], stage, b->advect));
+    LB_CUDA(launch_stage_batch(s, b->dcav(), b->drange(0), b->rblocks[0], stage, b->advect, b->rhs64));
     LB_CUDA(launch_assemble_batch(s, b->op, b->dcav(), b->drange(0), b->rblocks[0], stage,
                                   b->at<double>(b->lay.gpart)));
     BatchFinish none{0, 0.0, 0, 0, nullptr};
@@ -367,7 +366,8 @@ int build_graph(lc_batch *b) {
             rc = bcuda(e2, "cudaStreamEndCapture(body)");
             break;
         }
-        e = launch_thom_batch(s, b->dcav(), b->count, b->U);
+        e = b->rhs64 ? cudaSuccess : launch_psi32_batch(s, b->dcav(), b->drange(0), b->rblocks[0]);
+        if (e == cudaSuccess) e = launch_thom_batch(s, b->dcav(), b->count, b->U);
         if (e != cudaSuccess) rc = bcuda(e, "launch_thom_batch");
     }
     cudaGraph_t g = nullptr;
@@ -397,6 +397,7 @@ int eager_step(lc_batch *b) {
             LB_CUDA(cudaStreamSynchronize(s));
             if (!more) break;
         }
+        if (!b->rhs64) LB_CUDA(launch_psi32_batch(s, b->dcav(), b->drange(0), b->rblocks[0]));
         LB_CUDA(launch_thom_batch(s, b->dcav(), b->count, b->U));
     }
     return LC_OK;
@@ -478,7 +479,7 @@ lc_batch *lc_batch_create(int count, const int *N, const double *Re, const doubl
     for (int c = 0; c < count; ++c) {
         if (N[c] < 128 || N[c] > 8192 || nlevels(N[c]) < 2 || !(Re[c] > 0.0) || !std::isfinite(Re[c])) {
             delete b;
-            bfail(LC_ERR_ARG, "cavity " + std::to_string(c) + ": N must be 2^k or 3*2^k in 128..8192, Re > 0");
+            bfail(LC_ERR_ARG, "cavity " + std::to_string(c) + ": N must be 2^k, 3*2^k, 5*2^k or 7*2^k in 128..8192, Re > 0");
             return nullptr;
         }
         double h = 1.0 / N[c];
@@ -550,6 +551,9 @@ int lc_batch_set_option(lc_batch *b, const char *key, double v) {
     } else if (k == "advect") {
         if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "advect must be 0 or 1");
         b->advect = iv;
+    } else if (k == "rhs64") {
+        if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "rhs64 must be 0 or 1");
+        b->rhs64 = iv;
     } else if (k == "graph") {
         if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "graph must be 0 or 1");
         b->use_graph = iv;
@@ -759,6 +763,85 @@ int lc_batch_autotune(lc_batch *b, int reps, int *shapes_out, int max_levels) {
     b->dirty = true;
     for (int l = b->Lmax; l < max_levels; ++l) shapes_out[l] = -1;
     return rc;
+}
+
+int lc_batch_autotune_schedule(lc_batch *b, int steps, int nu_out[2]) {
+    LB_CHECK(b);
+    if (steps < 1 || !nu_out) return bfail(LC_ERR_ARG, "bad steps or output");
+    int rc = binit(b);
+    if (rc) return rc;
+    rc = bsync(b);  // report (and clear) an error from earlier work before timing
+    if (rc) return rc;
+    cudaStream_t s = b->stream();
+    void *save = nullptr;
+    LB_CUDA(cudaMalloc(&save, b->lay.total));
+    LB_CUDA(cudaMemcpyAsync(save, b->ws, b->lay.total, cudaMemcpyDeviceToDevice, s));
+    long long steps0 = b->steps;
+    std::vector<int> shape0 = b->shape;
+    int nu1_0 = b->nu1, nu2_0 = b->nu2;
+    static const int kCand[6][2] = {{1, 1}, {2, 1}, {1, 2}, {2, 2}, {3, 1}, {3, 2}};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 1e30f;
+    int pick = -1;
+    rc = LC_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        rc = bfail(LC_ERR_CUDA, "cudaEventCreate failed");
+    for (int k = 0; k < 6 && rc == LC_OK; ++k) {
+        b->nu1 = kCand[k][0];
+        b->nu2 = kCand[k][1];
+        b->shape.assign(b->Lmax, -1);
+        fill_tables(b);
+        rc = upload_tables(b);
+        if (rc) break;
+        b->dirty = true;
+        rc = lc_batch_step(b, 1);
+        if (rc) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) rc = bfail(LC_ERR_CUDA, "cudaEventRecord failed");
+        if (rc == LC_OK) rc = lc_batch_step(b, steps);
+        if (rc == LC_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = bfail(LC_ERR_CUDA, "cudaEventRecord failed");
+        if (rc) break;
+        int st = bsync(b);  // a schedule whose solves hit max_cycles is not a candidate
+        if (st == LC_ERR_CUDA) {
+            rc = st;
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = bfail(LC_ERR_CUDA, "cudaEventElapsedTime failed");
+            break;
+        }
+        if (st == LC_OK && ms < best) {
+            best = ms;
+            pick = k;
+        }
+        // back to the state the tuner started from
+        if (cudaMemcpyAsync(b->ws, save, b->lay.total, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            rc = bfail(LC_ERR_CUDA, "restoring the workspace failed");
+        b->steps = steps0;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaMemcpyAsync(b->ws, save, b->lay.total, cudaMemcpyDeviceToDevice, s);
+    cudaStreamSynchronize(s);
+    cudaFree(save);
+    b->steps = steps0;
+    if (rc == LC_OK && pick < 0) rc = bfail(LC_ERR_NOCONV, "no smoothing schedule converged");
+    if (rc == LC_OK) {
+        b->nu1 = kCand[pick][0];
+        b->nu2 = kCand[pick][1];
+        b->shape.assign(b->Lmax, -1);
+        nu_out[0] = b->nu1;
+        nu_out[1] = b->nu2;
+    } else {
+        b->nu1 = nu1_0;
+        b->nu2 = nu2_0;
+        b->shape = shape0;
+    }
+    fill_tables(b);
+    int rc2 = upload_tables(b);
+    b->dirty = true;
+    return rc ? rc : rc2;
 }
 
 }  // extern "C"

@@ -15,6 +15,10 @@
 // f - L_h psi = -rho / (kappa h^2), and full-weighting the fine residual onto
 // the coarse grid gives the coarse scaled right-hand side g_c = 4 R(rho).
 // Relative residual norms are scale-free: ||rho|| / ||g|| = ||f - L psi|| / ||f||.
+// Every kernel sums neighbours in the same order, (E + W) + (N + S) and
+// (NE + SE) + (NW + SW) (column pairs, which a kernel can share between
+// neighbouring columns), so all execution modes give the same bits and the
+// scheme stays exactly equivariant under the mirror x -> 1 - x.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -154,6 +158,12 @@ cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *
                                  FinishArgs fin);
 
 int residual_norm_blocks(int N);
+// nsw lexicographic SOR sweeps (Eq. (15) in its superscripts' order) in one
+// block, pipelined over wavefronts; psi in shared memory when
+// sor_smem_bytes(N, P) <= kMaxSmem.
+cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g, int N, int P, int nsw, double beta);
+size_t sor_smem_bytes(int N, int P);
+cudaError_t init_sor_kernel_attributes();
 int assemble_blocks(int N);
 int monitor_blocks(int N);
 
@@ -166,7 +176,8 @@ cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi
                            int N, int P, double *part, DevState *ds, double dt);
 cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P);
 
-// FP64 correction target of the mixed-precision fine level (psi64 == nullptr: none).
+// FP64 correction target of the mixed-precision fine level (psi64 == nullptr:
+// none; psi32 == nullptr: the FP32 shadow is refreshed after the solve).
 struct Correct64 {
     double *psi64;
     int P64;
@@ -175,10 +186,12 @@ struct Correct64 {
 };
 
 // ---- shared-memory multigrid kernels (lc_mg.cu)
-// Tile shapes of the shared-memory kernels: 0 = 128x64, 1 = 64x64, 2 = 32x32,
-// 3 = 16x16 owned nodes.  tile_shape_for picks one per level (force >= 0
-// overrides).
+// Tile shapes of the shared-memory kernels (owned nodes): 0 = 110x54,
+// 1 = 110x22, 2 = 46x22, 3 = 16x16.  tile_shape_for picks one per level
+// (force >= 0 overrides).
 int tile_shape_for(int N, int op, int nu, int elem, int force);
+int tile_tx(int shape);
+int tile_ty(int shape);
 int tiles_of(int N, int shape);
 size_t tile_smem_bytes(int shape, int op, int nu, int elem);
 size_t coarse_smem_bytes(int N0, int nl, int elem);
@@ -281,12 +294,13 @@ cudaError_t launch_up_batch(cudaStream_t s, int shape, int op, BatchCav *cav, co
 cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count, int smem, int nu1, int nu2, int nuc,
                                 float beta);
 cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
-                               int advect);
+                               int advect, int rhs64);
 cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
                                   double *gpart);
 cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks,
                                   double *rpart, const double *gpart, BatchFinish fin);
 cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U);
+cudaError_t launch_psi32_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks);
 cudaError_t launch_to32_batch(cudaStream_t s, BatchCav *cav, int c);
 
 // Sets the calling thread's lc_last_error() message.

@@ -57,7 +57,7 @@ template <typename T, int OP>
 __device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__restrict__ g, size_t c, int P) {
     T n4 = (psi[c + 1] + psi[c - 1]) + (psi[c + P] + psi[c - P]);
     if (OP == 1) {
-        T d4 = (psi[c + P + 1] + psi[c + P - 1]) + (psi[c - P + 1] + psi[c - P - 1]);
+        T d4 = (psi[c + P + 1] + psi[c - P + 1]) + (psi[c + P - 1] + psi[c - P - 1]);
         return fma(T(0.2), n4, fma(T(0.05), d4, g[c]));
     }
     return fma(T(0.25), n4, g[c]);
@@ -69,6 +69,10 @@ __device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__rest
 // never neighbour each other, so the phase is a Jacobi update of that colour.
 // Each thread updates two nodes of the colour in one column, rows j and j+2,
 // which share the loads of row j+1; RELAX = false is the beta = 1 update.
+// Compact: the lanes of a warp hold same-colour nodes two columns apart in one
+// row, so the diagonal sum d4 = V(i+1) + V(i-1), with the column sums
+// V(k) = psi(k, j+1) + psi(k, j-1), takes V(i-1) from the lane to the left
+// (the same additions in the same order as gs_value, one fewer per node).
 template <typename T, int OP, bool RELAX>
 __global__ void __launch_bounds__(kBX *kBY)
     k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
@@ -83,31 +87,49 @@ __global__ void __launch_bounds__(kBX *kBY)
         j = 1 + 4 * (b >> 1) + (b & 1);
         i = (((colour + j) & 1) ? 1 : 2) + 2 * a;
     }
+    if (OP == 1) {
+        // every lane of the warp reaches the shuffles; lanes past the grid
+        // load nothing and store nothing
+        bool rowok = j < N, ok = rowok && i < N;
+        bool second = ok && j + 2 < N;
+        size_t c = (size_t)j * P + i, c2 = c + 2 * (size_t)P;
+        bool colr = rowok && i + 1 <= N;  // column i + 1 exists (it may be the wall)
+        T m_e = colr ? psi[c + P + 1] : T(0);
+        T m_c = ok ? psi[c + P] : T(0);
+        T Vr = colr ? m_e + psi[c - P + 1] : T(0);
+        T V2r = (colr && j + 2 < N) ? psi[c2 + P + 1] + m_e : T(0);
+        T Vl = __shfl_up_sync(0xffffffffu, Vr, 1), V2l = __shfl_up_sync(0xffffffffu, V2r, 1);
+        if (!ok) return;
+        if (threadIdx.x == 0) {
+            T m_w = psi[c + P - 1];
+            Vl = m_w + psi[c - P - 1];
+            if (second) V2l = psi[c2 + P - 1] + m_w;
+        }
+        T n4 = (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]);
+        T v1 = fma(T(0.2), n4, fma(T(0.05), Vr + Vl, g[c])), v2 = T(0);
+        if (second) {
+            T n42 = (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c);
+            v2 = fma(T(0.2), n42, fma(T(0.05), V2r + V2l, g[c2]));
+        }
+        if (RELAX) {
+            T o1 = psi[c];
+            v1 = fma(beta, v1 - o1, o1);
+            if (second) {
+                T o2 = psi[c2];
+                v2 = fma(beta, v2 - o2, o2);
+            }
+        }
+        psi[c] = v1;
+        if (second) psi[c2] = v2;
+        return;
+    }
     if (i >= N || j >= N) return;
     size_t c = (size_t)j * P + i;
     bool second = j + 2 < N;
     size_t c2 = c + 2 * (size_t)P;
-    // shared row j + 1
-    T m_w = psi[c + P - 1], m_c = psi[c + P], m_e = psi[c + P + 1];
-    T v1, v2 = T(0);
-    {
-        T n4 = (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]);
-        if (OP == 1) {
-            T d4 = (m_e + m_w) + (psi[c - P + 1] + psi[c - P - 1]);
-            v1 = fma(T(0.2), n4, fma(T(0.05), d4, g[c]));
-        } else {
-            v1 = fma(T(0.25), n4, g[c]);
-        }
-    }
-    if (second) {
-        T n4 = (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c);
-        if (OP == 1) {
-            T d4 = (psi[c2 + P + 1] + psi[c2 + P - 1]) + (m_e + m_w);
-            v2 = fma(T(0.2), n4, fma(T(0.05), d4, g[c2]));
-        } else {
-            v2 = fma(T(0.25), n4, g[c2]);
-        }
-    }
+    T m_c = psi[c + P];  // shared row j + 1
+    T v1 = fma(T(0.25), (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]), g[c]), v2 = T(0);
+    if (second) v2 = fma(T(0.25), (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c), g[c2]);
     if (RELAX) {
         T o1 = psi[c];
         v1 = fma(beta, v1 - o1, o1);
@@ -175,8 +197,8 @@ __global__ void __launch_bounds__(kBX *kBY)
     psi[(size_t)j * Pf + i] += e;
 }
 
-// Coarsest grid (2 or 3 intervals: one or four unknowns): nsweeps colour
-// sweeps in one block.
+// Coarsest grid (2, 3, 5 or 7 intervals: at most 36 unknowns, one thread each
+// in a block of 64): nsweeps colour sweeps in one block.
 template <typename T, int OP>
 __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int nsweeps, T beta) {
     int n = N - 1;
@@ -198,6 +220,10 @@ __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, 
 }
 
 // Per-block partial sums of rho^2 over interior nodes (FP64 accumulation).
+// The column sums V(k) = psi(k, j+1) + psi(k, j-1) are formed once per column
+// and passed between neighbouring lanes (blockDim.x = 32: a warp is 32
+// consecutive columns of one row), so n4 = (E + W) + V(i) and
+// d4 = V(i+1) + V(i-1) cost 4 additions instead of 6, in gs_value's order.
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials,
@@ -206,9 +232,21 @@ __global__ void __launch_bounds__(kBX *kBY)
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     double v = 0.0;
-    if (i < N && j < N) {
-        size_t c = (size_t)j * P + i;
-        double r = (double)(gs_value<T, OP>(psi, g, c, P) - psi[c]);
+    bool rowok = j < N;
+    size_t c = (size_t)j * P + i;
+    T Vc = (rowok && i <= N) ? psi[c + P] + psi[c - P] : T(0);
+    T Vr = __shfl_down_sync(0xffffffffu, Vc, 1), Vl = __shfl_up_sync(0xffffffffu, Vc, 1);
+    if (rowok && i < N) {
+        T n4 = (psi[c + 1] + psi[c - 1]) + Vc;
+        T gs;
+        if (OP == 1) {
+            if (threadIdx.x == 31) Vr = psi[c + P + 1] + psi[c - P + 1];
+            if (threadIdx.x == 0) Vl = psi[c + P - 1] + psi[c - P - 1];
+            gs = fma(T(0.2), n4, fma(T(0.05), Vr + Vl, g[c]));
+        } else {
+            gs = fma(T(0.25), n4, g[c]);
+        }
+        double r = (double)(gs - psi[c]);
         v = r * r;
     }
     v = block_sum(v, sh);
@@ -418,9 +456,9 @@ cudaError_t launch_prolong_correct(cudaStream_t s, T *psi, int Nf, int Pf, const
 template <typename T>
 cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta) {
     if (op == 1)
-        k_coarsest<T, 1><<<1, 32, 0, s>>>(psi, g, N, P, nsweeps, beta);
+        k_coarsest<T, 1><<<1, 64, 0, s>>>(psi, g, N, P, nsweeps, beta);
     else
-        k_coarsest<T, 0><<<1, 32, 0, s>>>(psi, g, N, P, nsweeps, beta);
+        k_coarsest<T, 0><<<1, 64, 0, s>>>(psi, g, N, P, nsweeps, beta);
     return cudaGetLastError();
 }
 
@@ -478,6 +516,93 @@ cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi
 cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P) {
     k_zero_walls<<<(N + 1 + 255) / 256, 256, 0, s>>>(psi, N, P);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Lexicographic SOR, Eq. (15) in the order its n / n+1 superscripts fix: at
+// node (i, j) the neighbours (i-1, j-1), (i-1, j), (i-1, j+1) and (i, j-1)
+// already hold this sweep's values, the others the previous sweep's (i is the
+// outer loop, j the inner one).
+//
+// Wavefronts.  Number the interior nodes by t = W i + j (W = 2 compact, 1
+// 5-point).  Every new neighbour of (i, j) lies on an earlier front (t - 1 ..
+// t - 3) and every old one on a later front, and no two nodes of one front
+// are neighbours.  Updating the fronts in increasing t, each front all at
+// once, is therefore exactly the lexicographic sweep.  Sweep k + 1 may run D
+// fronts behind sweep k (D = 4 compact, 2 5-point: one more than the
+// stencil's reach in t), so nsw sweeps run as one pipelined pass of
+// (number of fronts) + D (nsw - 1) steps, one barrier per step.  The method
+// is sequential beyond a front, so one block does the pass; psi is updated in
+// place, in shared memory when the grid fits (SMEM) and in global memory
+// otherwise.  The node update is the smoother's expression.
+template <int OP>
+__device__ __forceinline__ double sor_value(const double *p, const double *__restrict__ g, size_t c, int P) {
+    double n4 = (p[c + 1] + p[c - 1]) + (p[c + P] + p[c - P]);
+    if (OP == 1) {
+        double d4 = (p[c + P + 1] + p[c - P + 1]) + (p[c + P - 1] + p[c - P - 1]);
+        return fma(0.2, n4, fma(0.05, d4, g[c]));
+    }
+    return fma(0.25, n4, g[c]);
+}
+
+template <int OP, bool SMEM>
+__global__ void __launch_bounds__(1024)
+    k_sor_lex(double *psi, const double *__restrict__ g, int N, int P, int nsw, double beta) {
+    extern __shared__ double sor_sp[];
+    double *p = SMEM ? sor_sp : psi;
+    const size_t nodes = (size_t)(N + 1) * P;
+    if (SMEM) {
+        for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) p[q] = psi[q];
+        __syncthreads();
+    }
+    constexpr int W = OP == 1 ? 2 : 1, D = OP == 1 ? 4 : 2;
+    const int t0 = W + 1, t1 = (W + 1) * (N - 1);
+    const int maxc = (N - 2) / W + 1;  // most nodes on one front
+    const int steps = (t1 - t0 + 1) + D * (nsw - 1);
+    for (int s = 0; s < steps; ++s) {
+        for (int q = threadIdx.x; q < nsw * maxc; q += blockDim.x) {
+            int k = q / maxc, r = q - k * maxc;
+            int t = t0 + s - D * k;
+            if (t < t0 || t > t1) continue;
+            int lo = t - (N - 1) > 0 ? (t - (N - 1) + W - 1) / W : 1;
+            if (lo < 1) lo = 1;
+            int i = lo + r, j = t - W * i;
+            if (i > N - 1 || j < 1) continue;
+            size_t c = (size_t)j * P + i;
+            double v = sor_value<OP>(p, g, c, P);
+            if (beta != 1.0) v = fma(beta, v - p[c], p[c]);
+            p[c] = v;
+        }
+        __syncthreads();
+    }
+    if (SMEM)
+        for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) psi[q] = p[q];
+}
+
+size_t sor_smem_bytes(int N, int P) { return (size_t)(N + 1) * P * sizeof(double); }
+
+cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g, int N, int P, int nsw, double beta) {
+    size_t sm = sor_smem_bytes(N, P);
+    bool fits = sm <= (size_t)kMaxSmem;
+    if (op == 1) {
+        if (fits)
+            k_sor_lex<1, true><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
+        else
+            k_sor_lex<1, false><<<1, 1024, 0, s>>>(psi, g, N, P, nsw, beta);
+    } else {
+        if (fits)
+            k_sor_lex<0, true><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
+        else
+            k_sor_lex<0, false><<<1, 1024, 0, s>>>(psi, g, N, P, nsw, beta);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t init_sor_kernel_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(k_sor_lex<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sor_lex<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    return e;
 }
 
 #define LCX_INSTANTIATE(T)                                                                                           \

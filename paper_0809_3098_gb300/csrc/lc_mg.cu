@@ -30,7 +30,7 @@ template <typename T, int OP>
 __device__ __forceinline__ T gs_local(const T *sp, const T *sg, int c, int LP) {
     T n4 = (sp[c + 1] + sp[c - 1]) + (sp[c + LP] + sp[c - LP]);
     if (OP == 1) {
-        T d4 = (sp[c + LP + 1] + sp[c + LP - 1]) + (sp[c - LP + 1] + sp[c - LP - 1]);
+        T d4 = (sp[c + LP + 1] + sp[c - LP + 1]) + (sp[c + LP - 1] + sp[c - LP - 1]);
         return fma(T(0.2), n4, fma(T(0.05), d4, sg[c]));
     }
     return fma(T(0.25), n4, sg[c]);
@@ -96,7 +96,7 @@ __device__ __forceinline__ T gs_pairs(const T *sp, const T *sg, int LP, int x, i
         row3<T>(r0 + LP, x, xodd, nw, n, ne);
         row3<T>(r0 - LP, x, xodd, sw, so, se);
         T n4 = (e + w) + (n + so);
-        T d4 = (ne + nw) + (se + sw);
+        T d4 = (ne + se) + (nw + sw);
         return fma(T(0.2), n4, fma(T(0.05), d4, sg[y * LP + x]));
     }
     T n = mid1<T>(r0 + LP, x, xodd), so = mid1<T>(r0 - LP, x, xodd);
@@ -104,46 +104,69 @@ __device__ __forceinline__ T gs_pairs(const T *sp, const T *sg, int LP, int x, i
     return fma(T(0.25), n4, sg[y * LP + x]);
 }
 
-// One colour phase over the tile's updatable nodes: local [1, LX-2] x
-// [1, LY-2] intersected with the domain interior.  Block is 2-D with
-// blockDim.x = 32, so a warp works on one row.
+// Updates a pair of same-colour nodes (x, y) and (x, y + 2) from pair loads:
+// rows y - 1 .. y + 3, row y + 1 shared; same operands and order as gs_local.
 template <typename T, int OP>
-__device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, int gy0, int N, int colour,
-                           T beta) {
+__device__ __forceinline__ void update_pair(T *sp, const T *sg, int LP, int x, int y, bool xodd, bool two, T beta) {
+    T *r0 = sp + y * LP;
+    T aw, ap, ae, bw, bp, be, cw, cp, ce;  // rows y - 1, y, y + 1
+    row3<T>(r0 - LP, x, xodd, aw, ap, ae);
+    row3<T>(r0, x, xodd, bw, bp, be);
+    row3<T>(r0 + LP, x, xodd, cw, cp, ce);
+    T v1;
+    if (OP == 1) {
+        T n4 = (be + bw) + (cp + ap);
+        T d4 = (ce + ae) + (cw + aw);
+        v1 = fma(T(0.2), n4, fma(T(0.05), d4, sg[y * LP + x]));
+    } else {
+        v1 = fma(T(0.25), (be + bw) + (cp + ap), sg[y * LP + x]);
+    }
+    if (beta != T(1)) v1 = fma(beta, v1 - bp, bp);
+    if (two) {
+        T dw, dp, de, ew, ep, ee;  // rows y + 2, y + 3
+        row3<T>(r0 + 2 * LP, x, xodd, dw, dp, de);
+        row3<T>(r0 + 3 * LP, x, xodd, ew, ep, ee);
+        T v2;
+        if (OP == 1) {
+            T n4 = (de + dw) + (ep + cp);
+            T d4 = (ee + ce) + (ew + cw);
+            v2 = fma(T(0.2), n4, fma(T(0.05), d4, sg[(y + 2) * LP + x]));
+        } else {
+            v2 = fma(T(0.25), (de + dw) + (ep + cp), sg[(y + 2) * LP + x]);
+        }
+        if (beta != T(1)) v2 = fma(beta, v2 - dp, dp);
+        r0[2 * LP + x] = v2;
+    }
+    r0[x] = v1;
+}
+
+// One colour phase over the tile's updatable nodes: local [1, LX-2] x
+// [1, LY-2] intersected with the domain interior ([xlo, xhi] x [ylo, yhi]).
+// Block is 2-D with blockDim.x = 32; each thread updates two nodes of the
+// colour in one column (rows y and y + 2).
+template <typename T, int OP>
+__device__ void tile_phase(T *sp, const T *sg, int LP, int xlo, int xhi, int ylo, int yhi, int gx0, int gy0,
+                           int colour, T beta) {
     if (OP == 1) {
         int pi = colour & 1, pj = colour >> 1;
-        int x0 = ((gx0 + 1) & 1) == pi ? 1 : 2;
-        int y0 = ((gy0 + 1) & 1) == pj ? 1 : 2;
+        int x0 = ((gx0 + xlo) & 1) == pi ? xlo : xlo + 1;  // first column of the colour
+        int y0 = ((gy0 + ylo) & 1) == pj ? ylo : ylo + 1;
         bool xodd = x0 & 1;
-        int nx = LX - 2 >= x0 ? (LX - 2 - x0) / 2 + 1 : 0;
-        int ny = LY - 2 >= y0 ? (LY - 2 - y0) / 2 + 1 : 0;
-        for (int yy = threadIdx.y; yy < ny; yy += blockDim.y) {
-            int y = y0 + 2 * yy, gj = gy0 + y;
-            if (gj < 1 || gj >= N) continue;
-            for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
-                int x = x0 + 2 * xx, gi = gx0 + x;
-                if (gi < 1 || gi >= N) continue;
-                T pc;
-                T v = gs_pairs<T, OP>(sp, sg, LP, x, y, xodd, pc);
-                if (beta != T(1)) v = fma(beta, v - pc, pc);
-                sp[y * LP + x] = v;
-            }
+        for (int y = y0 + 4 * (int)threadIdx.y; y <= yhi; y += 4 * blockDim.y) {
+            bool two = y + 2 <= yhi;
+            for (int x = x0 + 2 * (int)threadIdx.x; x <= xhi; x += 2 * blockDim.x)
+                update_pair<T, OP>(sp, sg, LP, x, y, xodd, two, beta);
         }
     } else {
-        int nx = (LX - 2) / 2 + 1;
-        for (int y = 1 + threadIdx.y; y <= LY - 2; y += blockDim.y) {
-            int gj = gy0 + y;
-            if (gj < 1 || gj >= N) continue;
-            int x0 = ((gx0 + 1 + gj) & 1) == colour ? 1 : 2;
+        // rows y and y + 2 share a parity: thread rows (ylo, ylo+2), (ylo+1, ylo+3), (ylo+4, ...)
+        for (int k = threadIdx.y; ; k += blockDim.y) {
+            int y = ylo + 4 * (k >> 1) + (k & 1);
+            if (y > yhi) break;
+            bool two = y + 2 <= yhi;
+            int x0 = ((gx0 + xlo + gy0 + y) & 1) == colour ? xlo : xlo + 1;
             bool xodd = x0 & 1;
-            for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) {
-                int x = x0 + 2 * xx, gi = gx0 + x;
-                if (x > LX - 2 || gi < 1 || gi >= N) continue;
-                T pc;
-                T v = gs_pairs<T, OP>(sp, sg, LP, x, y, xodd, pc);
-                if (beta != T(1)) v = fma(beta, v - pc, pc);
-                sp[y * LP + x] = v;
-            }
+            for (int x = x0 + 2 * (int)threadIdx.x; x <= xhi; x += 2 * blockDim.x)
+                update_pair<T, OP>(sp, sg, LP, x, y, xodd, two, beta);
         }
     }
 }
@@ -151,9 +174,12 @@ __device__ void tile_phase(T *sp, const T *sg, int LP, int LX, int LY, int gx0, 
 template <typename T, int OP>
 __device__ void tile_sweeps(T *sp, const T *sg, int LP, int LX, int LY, int gx0, int gy0, int N, int nu, T beta) {
     int ncol = OP == 1 ? 4 : 2;
+    // updatable local range: [1, L-2] and the domain interior [1, N-1]
+    int xlo = max(1, 1 - gx0), xhi = min(LX - 2, N - 1 - gx0);
+    int ylo = max(1, 1 - gy0), yhi = min(LY - 2, N - 1 - gy0);
     for (int s = 0; s < nu; ++s)
         for (int col = 0; col < ncol; ++col) {
-            tile_phase<T, OP>(sp, sg, LP, LX, LY, gx0, gy0, N, col, beta);
+            tile_phase<T, OP>(sp, sg, LP, xlo, xhi, ylo, yhi, gx0, gy0, col, beta);
             __syncthreads();
         }
 }
@@ -329,7 +355,7 @@ __device__ __forceinline__ double up_body(int bx, int by, const T *__restrict__ 
                 size_t c64 = (size_t)gj * cor.P64 + gi;
                 double pnew = cor.psi64[c64] + (double)sp[c];
                 cor.psi64[c64] = pnew;
-                cor.psi32[(size_t)gj * cor.P32 + gi] = (float)pnew;
+                if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + gi] = (float)pnew;
             } else {
                 psi_out[(size_t)gj * P + gi] = sp[c];
             }
@@ -493,7 +519,12 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-constexpr int kTBX = 32, kTBY = 16;  // 512 threads per tile block
+constexpr int kTBX = 32;
+// Threads per tile block: 32 x 16 for 54-row tiles, 32 x 8 otherwise, so that
+// with the compact operator and nu = 2 (halo 9 x 5) a colour phase's nodes
+// (at most 64 columns x 32 rows for 110 x 54, 32 x 16 for 46 x 22) fill whole
+// warps with two rows per thread.
+constexpr int tile_by(int TY) { return TY >= 54 ? 16 : 8; }
 
 // Shared memory of a tile kernel: psi and g tiles, plus k_up's coarse tile.
 template <typename T, int TX, int TY>
@@ -508,7 +539,7 @@ cudaError_t down_t(cudaStream_t s, const T *psi_in, int zero_init, const T *g, T
     size_t sm = down_smem<T, TX, TY>(OP, nu);
     auto kern = k_down<T, OP, TX, TY>;
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
-    kern<<<grid, dim3(kTBX, kTBY), sm, s>>>(psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+    kern<<<grid, dim3(kTBX, tile_by(TY)), sm, s>>>(psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
     return cudaGetLastError();
 }
 
@@ -518,7 +549,7 @@ cudaError_t up_t(cudaStream_t s, const T *psi_in, const T *g, const T *ec, int P
     size_t sm = down_smem<T, TX, TY>(OP, nu);
     auto kern = k_up<T, OP, TX, TY>;
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
-    kern<<<grid, dim3(kTBX, kTBY), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+    kern<<<grid, dim3(kTBX, tile_by(TY)), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
     return cudaGetLastError();
 }
 
@@ -545,7 +576,7 @@ __global__ void __launch_bounds__(512)
     const BatchCav &cv = cav[batch_locate(r, bx, by)];
     if (!cv.active) return;
     Correct64 cor{nullptr, 0, nullptr, 0};
-    if (level == 0) cor = Correct64{cv.psi64, cv.P[0], cv.psi32, cv.P[0]};
+    if (level == 0) cor = Correct64{cv.psi64, cv.P[0], nullptr, cv.P[0]};
     up_body<float, OP, TX, TY>(bx, by, cv.eB[level], cv.g32[level], cv.eA[level + 1], cv.P[level + 1], cv.eA[level],
                                cv.N >> level, cv.P[level], nu, beta, false, cor, smem_raw);
 }
@@ -560,10 +591,13 @@ __global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, i
                            beta, false, smem_raw);
 }
 
-constexpr int kShapeTX[4] = {128, 64, 32, 16};
-constexpr int kShapeTY[4] = {64, 64, 32, 16};
+constexpr int kShapeTX[4] = {110, 110, 46, 16};
+constexpr int kShapeTY[4] = {54, 22, 22, 16};
 
 }  // namespace
+
+int tile_tx(int shape) { return kShapeTX[shape]; }
+int tile_ty(int shape) { return kShapeTY[shape]; }
 
 int tiles_of(int N, int shape) {
     return ((N - 1 + kShapeTX[shape] - 1) / kShapeTX[shape]) * ((N - 1 + kShapeTY[shape] - 1) / kShapeTY[shape]);
@@ -610,9 +644,9 @@ template <typename T, int OP>
 cudaError_t down_shape(cudaStream_t s, int shape, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
                        T *gc, int Pc, int nu, T beta) {
     switch (shape) {
-        case 0: return down_t<T, OP, 128, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
-        case 1: return down_t<T, OP, 64, 64>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
-        case 2: return down_t<T, OP, 32, 32>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        case 0: return down_t<T, OP, 110, 54>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        case 1: return down_t<T, OP, 110, 22>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+        case 2: return down_t<T, OP, 46, 22>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
         default: return down_t<T, OP, 16, 16>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
     }
 }
@@ -621,9 +655,9 @@ template <typename T, int OP>
 cudaError_t up_shape(cudaStream_t s, int shape, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
                      int P, int nu, T beta, double *partials, Correct64 cor, FinishArgs fin) {
     switch (shape) {
-        case 0: return up_t<T, OP, 128, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
-        case 1: return up_t<T, OP, 64, 64>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
-        case 2: return up_t<T, OP, 32, 32>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        case 0: return up_t<T, OP, 110, 54>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        case 1: return up_t<T, OP, 110, 22>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+        case 2: return up_t<T, OP, 46, 22>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
         default: return up_t<T, OP, 16, 16>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
     }
 }
@@ -666,7 +700,7 @@ namespace {
 template <int OP, int TX, int TY>
 cudaError_t down_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
                          float beta) {
-    k_down_batch<OP, TX, TY><<<nblocks, dim3(kTBX, kTBY), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
+    k_down_batch<OP, TX, TY><<<nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
                                                                                                  beta);
     return cudaGetLastError();
 }
@@ -674,7 +708,7 @@ cudaError_t down_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int
 template <int OP, int TX, int TY>
 cudaError_t up_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
                        float beta) {
-    k_up_batch<OP, TX, TY><<<nblocks, dim3(kTBX, kTBY), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
+    k_up_batch<OP, TX, TY><<<nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
                                                                                                beta);
     return cudaGetLastError();
 }
@@ -683,9 +717,9 @@ template <int OP>
 cudaError_t down_batch_shape(cudaStream_t s, int shape, BatchCav *cav, const BatchRange *r, int level, int nb, int nu,
                              float beta) {
     switch (shape) {
-        case 0: return down_batch_t<OP, 128, 64>(s, cav, r, level, nb, nu, beta);
-        case 1: return down_batch_t<OP, 64, 64>(s, cav, r, level, nb, nu, beta);
-        case 2: return down_batch_t<OP, 32, 32>(s, cav, r, level, nb, nu, beta);
+        case 0: return down_batch_t<OP, 110, 54>(s, cav, r, level, nb, nu, beta);
+        case 1: return down_batch_t<OP, 110, 22>(s, cav, r, level, nb, nu, beta);
+        case 2: return down_batch_t<OP, 46, 22>(s, cav, r, level, nb, nu, beta);
         default: return down_batch_t<OP, 16, 16>(s, cav, r, level, nb, nu, beta);
     }
 }
@@ -694,9 +728,9 @@ template <int OP>
 cudaError_t up_batch_shape(cudaStream_t s, int shape, BatchCav *cav, const BatchRange *r, int level, int nb, int nu,
                            float beta) {
     switch (shape) {
-        case 0: return up_batch_t<OP, 128, 64>(s, cav, r, level, nb, nu, beta);
-        case 1: return up_batch_t<OP, 64, 64>(s, cav, r, level, nb, nu, beta);
-        case 2: return up_batch_t<OP, 32, 32>(s, cav, r, level, nb, nu, beta);
+        case 0: return up_batch_t<OP, 110, 54>(s, cav, r, level, nb, nu, beta);
+        case 1: return up_batch_t<OP, 110, 22>(s, cav, r, level, nb, nu, beta);
+        case 2: return up_batch_t<OP, 46, 22>(s, cav, r, level, nb, nu, beta);
         default: return up_batch_t<OP, 16, 16>(s, cav, r, level, nb, nu, beta);
     }
 }
@@ -731,11 +765,11 @@ cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count
 template <typename T>
 static cudaError_t set_attrs_t() {
     const void *k[] = {
-        (const void *)k_down<T, 0, 128, 64>, (const void *)k_down<T, 1, 128, 64>, (const void *)k_down<T, 0, 64, 64>,
-        (const void *)k_down<T, 1, 64, 64>,  (const void *)k_down<T, 0, 32, 32>,  (const void *)k_down<T, 1, 32, 32>,
-        (const void *)k_down<T, 0, 16, 16>,  (const void *)k_down<T, 1, 16, 16>,  (const void *)k_up<T, 0, 128, 64>,
-        (const void *)k_up<T, 1, 128, 64>,   (const void *)k_up<T, 0, 64, 64>,    (const void *)k_up<T, 1, 64, 64>,
-        (const void *)k_up<T, 0, 32, 32>,    (const void *)k_up<T, 1, 32, 32>,    (const void *)k_up<T, 0, 16, 16>,
+        (const void *)k_down<T, 0, 110, 54>, (const void *)k_down<T, 1, 110, 54>, (const void *)k_down<T, 0, 110, 22>,
+        (const void *)k_down<T, 1, 110, 22>,  (const void *)k_down<T, 0, 46, 22>,  (const void *)k_down<T, 1, 46, 22>,
+        (const void *)k_down<T, 0, 16, 16>,  (const void *)k_down<T, 1, 16, 16>,  (const void *)k_up<T, 0, 110, 54>,
+        (const void *)k_up<T, 1, 110, 54>,   (const void *)k_up<T, 0, 110, 22>,    (const void *)k_up<T, 1, 110, 22>,
+        (const void *)k_up<T, 0, 46, 22>,    (const void *)k_up<T, 1, 46, 22>,    (const void *)k_up<T, 0, 16, 16>,
         (const void *)k_up<T, 1, 16, 16>,    (const void *)k_coarse<T, 0>,        (const void *)k_coarse<T, 1>};
     for (const void *f : k) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
@@ -746,10 +780,10 @@ static cudaError_t set_attrs_t() {
 
 template <int OP>
 static cudaError_t set_batch_attrs_t() {
-    const void *k[] = {(const void *)k_down_batch<OP, 128, 64>, (const void *)k_down_batch<OP, 64, 64>,
-                       (const void *)k_down_batch<OP, 32, 32>,  (const void *)k_down_batch<OP, 16, 16>,
-                       (const void *)k_up_batch<OP, 128, 64>,   (const void *)k_up_batch<OP, 64, 64>,
-                       (const void *)k_up_batch<OP, 32, 32>,    (const void *)k_up_batch<OP, 16, 16>,
+    const void *k[] = {(const void *)k_down_batch<OP, 110, 54>, (const void *)k_down_batch<OP, 110, 22>,
+                       (const void *)k_down_batch<OP, 46, 22>,  (const void *)k_down_batch<OP, 16, 16>,
+                       (const void *)k_up_batch<OP, 110, 54>,   (const void *)k_up_batch<OP, 110, 22>,
+                       (const void *)k_up_batch<OP, 46, 22>,    (const void *)k_up_batch<OP, 16, 16>,
                        (const void *)k_coarse_batch<OP>};
     for (const void *f : k) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));

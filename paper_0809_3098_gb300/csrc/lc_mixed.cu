@@ -35,34 +35,70 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// FP64 scaled residual rho = (Gauss-Seidel value) - psi at interior nodes,
-// stored rounded to FP32 as the right-hand side of the FP32 correction cycle
-// (in the scaled form the correction equation's right-hand side is rho
-// itself), with per-block partial sums of rho^2 for the stopping test.
+// FP64 scaled residual rho = (Gauss-Seidel value) - psi at node (i, j) of a
+// warp that covers 32 consecutive columns of one row (blockDim.x = 32; every
+// lane calls this).  The column sums V(k) = psi(k, j+1) + psi(k, j-1) are
+// computed once and passed between neighbouring lanes, so that
+// n4 = (E + W) + V(i) and d4 = V(i+1) + V(i-1), in the order of every other
+// kernel.  Returns whether (i, j) is an interior node.
+template <int OP>
+__device__ __forceinline__ bool rho64_shared(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
+                                             int i, int j, double &rho) {
+    bool rowok = j < N;
+    size_t c = (size_t)j * P + i;
+    double Vc = (rowok && i <= N) ? psi[c + P] + psi[c - P] : 0.0;
+    double Vr = __shfl_down_sync(0xffffffffu, Vc, 1), Vl = __shfl_up_sync(0xffffffffu, Vc, 1);
+    bool act = rowok && i < N;
+    if (!act) return false;
+    double n4 = (psi[c + 1] + psi[c - 1]) + Vc;
+    double gs;
+    if (OP == 1) {
+        if (threadIdx.x == 31) Vr = psi[c + P + 1] + psi[c - P + 1];
+        if (threadIdx.x == 0) Vl = psi[c + P - 1] + psi[c - P - 1];
+        gs = fma(0.2, n4, fma(0.05, Vr + Vl, g[c]));
+    } else {
+        gs = fma(0.25, n4, g[c]);
+    }
+    rho = gs - psi[c];
+    return true;
+}
+
+__device__ __forceinline__ float block_sum_f(float v, float *sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int t = threadIdx.y * blockDim.x + threadIdx.x;
+    int lane = t & 31, warp = t >> 5, nw = (blockDim.x * blockDim.y + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    float r = 0.0f;
+    if (warp == 0) {
+        r = lane < nw ? sh[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_down_sync(0xffffffffu, r, o);
+    }
+    return r;
+}
+
+// FP64 residual rounded to FP32 as the right-hand side of the FP32 correction
+// cycle (in the scaled form the correction equation's right-hand side is rho
+// itself), with per-block partial sums of rho^2 for the stopping test.  The
+// squares are summed in FP32: they only decide when to stop, and a relative
+// error of 1e-7 in ||rho|| shifts the threshold by as much.
 template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual64_to32(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
                       float *__restrict__ r32, int P32, double *__restrict__ partials, FinishArgs fin) {
-    __shared__ double sh[32];
+    __shared__ float sh[32];
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    double v = 0.0;
-    if (i < N && j < N) {
-        size_t c = (size_t)j * P + i;
-        double n4 = (psi[c + 1] + psi[c - 1]) + (psi[c + P] + psi[c - P]);
-        double gs;
-        if (OP == 1) {
-            double d4 = (psi[c + P + 1] + psi[c + P - 1]) + (psi[c - P + 1] + psi[c - P - 1]);
-            gs = fma(0.2, n4, fma(0.05, d4, g[c]));
-        } else {
-            gs = fma(0.25, n4, g[c]);
-        }
-        double rho = gs - psi[c];
-        r32[(size_t)j * P32 + i] = (float)rho;
-        v = rho * rho;
+    float v = 0.0f;
+    double rho;
+    if (rho64_shared<OP>(psi, g, N, P, i, j, rho)) {
+        float r = (float)rho;
+        r32[(size_t)j * P32 + i] = r;
+        v = r * r;
     }
-    v = block_sum(v, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = v;
+    v = block_sum_f(v, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = (double)v;
     if (fin.enabled) finish_if_last(partials, fin);
 }
 
@@ -75,7 +111,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     size_t c = (size_t)j * P64 + i;
     double p = psi[c] + (double)e[(size_t)j * Pe + i];
     psi[c] = p;
-    psi32[(size_t)j * P32 + i] = (float)p;
+    if (psi32) psi32[(size_t)j * P32 + i] = (float)p;
 }
 
 // L(omega) in FP32 from the FP32 shadows, stage combination in FP64 (see
@@ -170,6 +206,9 @@ __global__ void k_to32(const double *__restrict__ src, int P64, float *__restric
 __device__ __forceinline__ int stage_in(int s) { return s == 0 ? 0 : (s & 1 ? 1 : 2); }     // 0,1,2,1,2
 __device__ __forceinline__ int stage_out(int s) { return s == 4 ? 0 : (s & 1 ? 2 : 1); }   // 1,2,1,2,0
 
+// RHS64: L(omega) in FP64 from psi64 and the FP64 stage vorticity (the
+// shadows are then neither read nor written), as the FP64 step computes it.
+template <bool RHS64>
 __global__ void __launch_bounds__(kBX *kBY)
     k_stage_batch(const BatchCav *cav, const BatchRange *r, int stage, StageCoef k, int advect) {
     int bx, by;
@@ -178,22 +217,36 @@ __global__ void __launch_bounds__(kBX *kBY)
     int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
     if (i >= N || j >= N) return;
     size_t c = (size_t)j * P + i;
-    const float *in32 = cv.Ws[stage_in(stage)], *psi = cv.psi32;
     const double *in64 = cv.W[stage_in(stage)], *W0 = cv.W[0];
     double *acc = cv.W[3], *out64 = cv.W[stage_out(stage)];
-    float *out32 = cv.Ws[stage_out(stage)];
-    float inv2h = (float)(0.5 * N);
-    float nu_invh2 = (float)((double)N * (double)N / cv.Re);
-    float wP = in32[c], wE = in32[c + 1], wW = in32[c - 1], wN = in32[c + P], wS = in32[c - P];
-    float L = nu_invh2 * fmaf(-4.0f, wP, (wE + wW) + (wN + wS));
-    if (advect) {
-        float u = (psi[c + P] - psi[c - P]) * inv2h;
-        float v = -(psi[c + 1] - psi[c - 1]) * inv2h;
-        float tx = u * ((wE - wW) * inv2h);
-        float ty = v * ((wN - wS) * inv2h);
-        L = (L - tx) - ty;
+    double Ld, wPd = in64[c];
+    if (RHS64) {
+        const double *psi = cv.psi64;
+        double inv2h = 0.5 * N, nu_invh2 = (double)N * (double)N / cv.Re;
+        double wE = in64[c + 1], wW = in64[c - 1], wN = in64[c + P], wS = in64[c - P];
+        Ld = nu_invh2 * fma(-4.0, wPd, (wE + wW) + (wN + wS));
+        if (advect) {
+            double u = (psi[c + P] - psi[c - P]) * inv2h;
+            double v = -(psi[c + 1] - psi[c - 1]) * inv2h;
+            double tx = u * ((wE - wW) * inv2h);
+            double ty = v * ((wN - wS) * inv2h);
+            Ld = (Ld - tx) - ty;
+        }
+    } else {
+        const float *in32 = cv.Ws[stage_in(stage)], *psi = cv.psi32;
+        float inv2h = (float)(0.5 * N);
+        float nu_invh2 = (float)((double)N * (double)N / cv.Re);
+        float wP = in32[c], wE = in32[c + 1], wW = in32[c - 1], wN = in32[c + P], wS = in32[c - P];
+        float L = nu_invh2 * fmaf(-4.0f, wP, (wE + wW) + (wN + wS));
+        if (advect) {
+            float u = (psi[c + P] - psi[c - P]) * inv2h;
+            float v = -(psi[c + 1] - psi[c - 1]) * inv2h;
+            float tx = u * ((wE - wW) * inv2h);
+            float ty = v * ((wN - wS) * inv2h);
+            L = (L - tx) - ty;
+        }
+        Ld = (double)L;
     }
-    double Ld = (double)L, wPd = in64[c];
     double bdt = k.bdt * cv.dt, o;
     if (k.mode == 3) {
         o = fma(bdt, Ld, fma(k.a1, wPd, acc[c]));
@@ -203,7 +256,7 @@ __global__ void __launch_bounds__(kBX *kBY)
         else if (k.mode == 2) acc[c] = fma(k.acc_L * cv.dt, Ld, fma(k.acc_in, wPd, acc[c]));
     }
     out64[c] = o;
-    out32[c] = (float)o;
+    if (!RHS64) cv.Ws[stage_out(stage)][c] = (float)o;
 }
 
 // Poisson right-hand side (as k_assemble_rhs) of every cavity's new stage
@@ -246,31 +299,23 @@ __global__ void __launch_bounds__(kBX *kBY)
     k_residual_batch(BatchCav *cav, const BatchRange *r, double *__restrict__ rpart, const double *__restrict__ gpart,
                      BatchFinish fin) {
     __shared__ double sh[32];
+    __shared__ float shf[32];
     __shared__ unsigned int s_last;
     int bx, by;
     int ci = batch_locate(r, bx, by);
     BatchCav &cv = cav[ci];
     int N = cv.N, P = cv.P[0];
     int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
-    double v = 0.0;
-    if (cv.active && i < N && j < N) {
-        const double *psi = cv.psi64, *g = cv.g64;
-        size_t c = (size_t)j * P + i;
-        double n4 = (psi[c + 1] + psi[c - 1]) + (psi[c + P] + psi[c - P]);
-        double gs;
-        if (OP == 1) {
-            double d4 = (psi[c + P + 1] + psi[c + P - 1]) + (psi[c - P + 1] + psi[c - P - 1]);
-            gs = fma(0.2, n4, fma(0.05, d4, g[c]));
-        } else {
-            gs = fma(0.25, n4, g[c]);
-        }
-        double rho = gs - psi[c];
-        cv.g32[0][c] = (float)rho;
-        v = rho * rho;
+    float v = 0.0f;
+    double rho;
+    if (cv.active && rho64_shared<OP>(cv.psi64, cv.g64, N, P, i, j, rho)) {
+        float rf = (float)rho;
+        cv.g32[0][(size_t)j * P + i] = rf;
+        v = rf * rf;
     }
-    v = block_sum(v, sh);
+    v = block_sum_f(v, shf);
     int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
-    if (tid == 0) rpart[blockIdx.x] = v;
+    if (tid == 0) rpart[blockIdx.x] = (double)v;
     if (!fin.enabled) return;
     int b0 = r->start[ci], nb = r->start[ci + 1] - b0;
     __syncthreads();
@@ -326,6 +371,18 @@ __global__ void __launch_bounds__(kBX *kBY)
         fin.bs->more = (int)any;
 }
 
+// FP32 shadow of every cavity's psi64 after its solve (read only by the next
+// stage's FP32 L(omega)).
+__global__ void __launch_bounds__(kBX *kBY) k_psi32_batch(const BatchCav *cav, const BatchRange *r) {
+    int bx, by;
+    const BatchCav &cv = cav[batch_locate(r, bx, by)];
+    int N = cv.N, P = cv.P[0];
+    int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
+    if (i >= N || j >= N) return;
+    size_t c = (size_t)j * P + i;
+    cv.psi32[c] = (float)cv.psi64[c];
+}
+
 // Thom's wall vorticity for every cavity (blockIdx.y = cavity), uniform lid U.
 __global__ void k_thom_batch(const BatchCav *cav, double U) {
     const BatchCav &cv = cav[blockIdx.y];
@@ -369,7 +426,7 @@ __global__ void k_thom_batch(const BatchCav *cav, double U) {
 }  // namespace
 
 cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
-                               int advect) {
+                               int advect, int rhs64) {
     // SSPRK(5,4) stage coefficients, Eqs. (9)-(13): bdt and acc_L are scaled by each cavity's dt in the kernel
     static const StageCoef kc[5] = {
         {1.0, 0.0, 0.391752226571890, 0.0, 0.0, 0},
@@ -377,7 +434,10 @@ cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *
         {0.620101851488403, 0.379898148511597, 0.251891774271694, 0.517231671970585, 0.0, 1},
         {0.178079954393132, 0.821920045606868, 0.544974750228521, 0.096059710526147, 0.063692468666290, 2},
         {0.0, 0.386708617503269, 0.226007483236906, 0.0, 0.0, 3}};
-    k_stage_batch<<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
+    if (rhs64)
+        k_stage_batch<true><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
+    else
+        k_stage_batch<false><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
     return cudaGetLastError();
 }
 
@@ -396,6 +456,11 @@ cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const B
         k_residual_batch<1><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
     else
         k_residual_batch<0><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_psi32_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks) {
+    k_psi32_batch<<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r);
     return cudaGetLastError();
 }
 

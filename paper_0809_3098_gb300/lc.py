@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
         "lc_batch_synchronize": ([vp], ci),
         "lc_batch_info": ([vp, ci, _dp], ci),
         "lc_batch_autotune": ([vp, ci, ctypes.POINTER(ci), ci], ci),
+        "lc_batch_autotune_schedule": ([vp, ci, ctypes.POINTER(ci)], ci),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -407,6 +408,12 @@ class Batch:
         shapes = (ctypes.c_int * 16)()
         _check(lib().lc_batch_autotune(self._h, reps, shapes, 16), "lc_batch_autotune")
         return [s for s in shapes if s >= 0]
+
+    def autotune_schedule(self, steps: int = 2) -> tuple:
+        """Picks the fastest smoothing schedule (nu1, nu2); see lc.h."""
+        nu = (ctypes.c_int * 2)()
+        _check(lib().lc_batch_autotune_schedule(self._h, steps, nu), "lc_batch_autotune_schedule")
+        return nu[0], nu[1]
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -9,7 +9,8 @@ centreline u(y) at x = 1/2 and the horizontal centreline v(x) at y = 1/2
 (central differences of psi, Eq. (22); wall values by the boundary
 conditions), and both paths' step times.  The mixed runs go through the
 batched engine (all Re in one launch per step), which gives the bits of
-single-cavity mixed runs.
+single-cavity mixed runs, once with the FP32 L(omega) stencils (the default)
+and once with L(omega) in FP64 (option rhs64).
 
     python -m tests.studies.precision_study --steps 20000 [--N 1024] > precision.json
 """
@@ -58,6 +59,13 @@ def main():
     batch.step(args.steps)
     batch.synchronize()
     t_mixed = time.perf_counter() - t0
+    # the same with L(omega) in FP64 (option rhs64): separates the error of
+    # the FP32 stencils from that of the FP32 multigrid corrections
+    t0 = time.perf_counter()
+    batch64 = lc.Batch([args.N] * len(args.Re), args.Re, rhs64=1)
+    batch64.step(args.steps)
+    batch64.synchronize()
+    t_mixed64 = time.perf_counter() - t0
     for c, Re in enumerate(args.Re):
         t1 = time.perf_counter()
         ref = lc.Cavity(args.N, Re, monitor=1)
@@ -73,11 +81,15 @@ def main():
         t_fp64 = time.perf_counter() - t1
         p64, w64 = ref.psi(), ref.omega()
         pm, wm = batch.psi(c), batch.omega(c)
+        pr, wr = batch64.psi(c), batch64.omega(c)
         u64, v64 = centrelines(p64)
         um, vm = centrelines(pm)
+        ur, vr = centrelines(pr)
         row = {"Re": Re, "dt": ref.params["dt"], "t_end": ref.params["dt"] * args.steps,
                "rel_err": {"psi": rel(pm, p64), "omega": rel(wm, w64), "u_centre": rel(um, u64),
                            "v_centre": rel(vm, v64)},
+               "rel_err_rhs64": {"psi": rel(pr, p64), "omega": rel(wr, w64), "u_centre": rel(ur, u64),
+                                 "v_centre": rel(vr, v64)},
                "psi_min": float(p64.min()), "fp64_seconds": t_fp64, "fp64_monitors": monitors,
                "vcycles_per_solve": {"fp64": float(ref.cycle_log().mean()),
                                      "mixed": float(batch.cycle_log(c).mean())}}
@@ -85,6 +97,7 @@ def main():
         ref.close()
         print(json.dumps(row), file=sys.stderr, flush=True)
     out["mixed_batch_seconds"] = t_mixed
+    out["mixed_rhs64_batch_seconds"] = t_mixed64
     print(json.dumps(out))
 
 

@@ -44,7 +44,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_create_validates_arguments(L):
-    assert not L.lc_create(20, 100.0, 0.0, 1e-10)      # 20 = 4 * 5
+    assert not L.lc_create(44, 100.0, 0.0, 1e-10)      # 44 = 4 * 11
     assert "N must be" in lc.last_error()
     assert not L.lc_create(16, -5.0, 0.0, 1e-10)
     assert not L.lc_create(16, 100.0, 0.0, 0.0)
@@ -79,7 +79,8 @@ def test_options_validate_without_gpu(L):
 
 
 def test_workspace_bytes(L):
-    assert lc.lc_workspace_bytes(20, 0) == 0
+    assert lc.lc_workspace_bytes(44, 0) == 0          # 44 = 4 * 11 is not a valid size
+    assert lc.lc_workspace_bytes(20, 0) > 0           # 20 = 4 * 5 is
     a, b = lc.lc_workspace_bytes(512, 0), lc.lc_workspace_bytes(1024, 0)
     assert 3.5 < b / a < 4.5
     assert b % 256 == 0

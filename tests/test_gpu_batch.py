@@ -23,7 +23,7 @@ def singles(Ns, Res, steps, **opts):
 
 @pytest.mark.parametrize("op", [lc.LC_OP_COMPACT, lc.LC_OP_5PT])
 def test_batch_bitwise_equals_single_contexts(op):
-    Ns, Res = [128, 192, 256, 384], [1000.0, 3000.0, 12000.0, 25000.0]
+    Ns, Res = [128, 192, 224, 256, 320, 384], [1000.0, 3000.0, 5000.0, 12000.0, 15000.0, 25000.0]
     b = lc.Batch(Ns, Res, op=op)
     b.step(3)
     ref = singles(Ns, Res, 3, op=op)
@@ -47,6 +47,27 @@ def test_batch_eager_equals_graph_and_autotune_keeps_bits():
         assert np.array_equal(a.psi(c), e.psi(c)) and np.array_equal(a.omega(c), e.omega(c))
         assert np.array_equal(a.psi(c), t.psi(c)) and np.array_equal(a.omega(c), t.omega(c))
         assert np.array_equal(a.cycle_log(c), t.cycle_log(c))
+
+
+def test_schedule_autotuner_restores_state_and_sets_schedule():
+    """After the schedule search the batch is back at its starting state and
+    steps exactly like a fresh batch given the chosen (nu1, nu2)."""
+    Ns, Res = [128, 256, 384], [1500.0, 8000.0, 25000.0]
+    t = lc.Batch(Ns, Res)
+    t.step(2)
+    ref_state = [(t.psi(c), t.omega(c)) for c in range(3)]
+    nu1, nu2 = t.autotune_schedule(steps=2)
+    assert (nu1, nu2) in {(1, 1), (2, 1), (1, 2), (2, 2), (3, 1), (3, 2)}
+    for c in range(3):
+        assert np.array_equal(t.psi(c), ref_state[c][0]) and np.array_equal(t.omega(c), ref_state[c][1])
+    assert t.info(0)["steps"] == 2
+    t.step(2)
+    f = lc.Batch(Ns, Res, nu1=nu1, nu2=nu2)
+    for c in range(3):
+        f.set_state(c, *ref_state[c])
+    f.step(2)
+    for c in range(3):
+        assert np.array_equal(t.psi(c), f.psi(c)) and np.array_equal(t.omega(c), f.omega(c))
 
 
 def test_batch_set_state_and_dt():
@@ -74,6 +95,16 @@ def test_batch_of_32_uneven_cavities_matches_singles():
         ref = singles([Ns[c]], [Res[c]], 2)[0]
         assert np.array_equal(b.cycle_log(c), ref[2])
         assert np.array_equal(b.psi(c), ref[0]) and np.array_equal(b.omega(c), ref[1])
+
+
+def test_batch_rhs64_bitwise_equals_single_contexts():
+    Ns, Res = [128, 320, 256], [2000.0, 15000.0, 30000.0]
+    b = lc.Batch(Ns, Res, rhs64=1)
+    b.step(3)
+    ref = singles(Ns, Res, 3, rhs64=1)
+    for c, (p, w, cyc) in enumerate(ref):
+        assert np.array_equal(b.cycle_log(c), cyc), c
+        assert np.array_equal(b.psi(c), p) and np.array_equal(b.omega(c), w), c
 
 
 def test_batch_errors():

@@ -21,7 +21,7 @@ def rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("N", [16, 24, 64, 128])
+@pytest.mark.parametrize("N", [16, 24, 40, 56, 64, 128])
 @pytest.mark.parametrize("op", [lc.LC_OP_5PT, lc.LC_OP_COMPACT])
 def test_mixed_matches_oracle(N, op):
     Re, steps = 1000.0, 5
@@ -34,6 +34,21 @@ def test_mixed_matches_oracle(N, op):
     assert g.residual() <= 1e-10
     gl, rl = g.cycle_log(), r.cycle_log()
     assert len(gl) == 5 * steps and np.abs(gl - rl).max() <= 2
+
+
+@pytest.mark.parametrize("N", [64, 128])
+@pytest.mark.parametrize("op", [lc.LC_OP_5PT, lc.LC_OP_COMPACT])
+def test_mixed_rhs64_matches_oracle(N, op):
+    """FP64 L(omega) inside the mixed step: the only difference from the FP64
+    step left is the Poisson iterate (both stop at the same FP64 residual)."""
+    Re, steps = 1000.0, 5
+    dt = dt_rule(N, Re)
+    g = lc.Cavity(N, Re, dt, 1e-10, op=op, precision=MIXED, rhs64=1)
+    r = oracle.Cavity(N, Re, dt, 1e-10, op=op)
+    g.step(steps)
+    r.step(steps)
+    assert rel(g.psi(), r.psi()) < 1e-7 and rel(g.omega(), r.omega()) < 1e-7
+    assert g.residual() <= 1e-10
 
 
 @pytest.mark.parametrize("coarse_max", [2, 16, 64, 256])

@@ -29,7 +29,7 @@ def pair(N, Re, op, tol=1e-10, **opts):
     return g, r
 
 
-@pytest.mark.parametrize("N", [8, 16, 24, 32, 48, 96])
+@pytest.mark.parametrize("N", [8, 10, 14, 16, 20, 24, 28, 32, 40, 48, 56, 96])
 @pytest.mark.parametrize("opname", ["5pt", "compact"])
 def test_small_grids_match_oracle(N, opname):
     g, r = pair(N, 400.0, OPS[opname])
@@ -171,7 +171,7 @@ def test_max_cycles_reports_noconv():
 
 def test_invalid_arguments():
     with pytest.raises(lc.LCError):
-        lc.Cavity(20, 100.0)
+        lc.Cavity(44, 100.0)  # 44 = 4 * 11 does not coarsen to 2, 3, 5 or 7
     g = lc.Cavity(16, 100.0)
     with pytest.raises(lc.LCError):
         g.set_option("nu1", 0)
@@ -214,14 +214,14 @@ MODES = {
     "tiles": dict(blocked=1, fine_phases=0, coarse_max=2),
     "tiles+fine-phases": dict(blocked=1, fine_phases=1, coarse_max=4),
     "coarse-block": dict(blocked=1, fine_phases=0, coarse_max=64),
-    "tiles128x64": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0),
-    "tiles64x64": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1),
+    "tiles110x54": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0),
+    "tiles110x22": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1),
     "tiles16x16": dict(blocked=1, fine_phases=0, coarse_max=2, tile_shape=3),
 }
 
 
 @pytest.mark.parametrize("mode", sorted(MODES))
-@pytest.mark.parametrize("N", [16, 24, 48, 128])
+@pytest.mark.parametrize("N", [16, 24, 48, 112, 128, 160])
 @pytest.mark.parametrize("opname", ["5pt", "compact"])
 def test_execution_modes_match_oracle(mode, N, opname):
     dt = dt_rule(N, 800.0)
@@ -233,7 +233,7 @@ def test_execution_modes_match_oracle(mode, N, opname):
     assert np.array_equal(g.cycle_log(), r.cycle_log())
 
 
-@pytest.mark.parametrize("N", [256, 384])
+@pytest.mark.parametrize("N", [224, 256, 320, 384])
 def test_execution_modes_are_bitwise_identical(N):
     """Tiles recompute halos with the same per-node expression, so every mode
     gives the same bits (a halo too small would show up here)."""
