@@ -136,7 +136,10 @@ const char *lc_last_error(void);
  *                 in a single thread block (default -1: 32 for FP64, 64 for
  *                 mixed precision), 2..256.
  *   "tile_shape"  -1 (default) picks each level's tile shape; 0..3 forces
- *                 110x54, 110x22, 46x22 or 16x16 owned nodes per tile.
+ *                 the shared-memory tiles of 110x54, 110x22, 46x22 or 16x16
+ *                 owned nodes, 4 the 44x20 register tiles held by one warp
+ *                 each (mixed precision, nu1, nu2 <= 2 with the compact
+ *                 operator; elsewhere a forced 4 falls back to the default).
  *   "graph"       1 (default) replays each step as one CUDA graph whose
  *                 V-cycle loops are device-side while-nodes; 0 launches the
  *                 same kernels one by one and drives the V-cycle loop from the

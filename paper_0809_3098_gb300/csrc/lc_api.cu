@@ -706,7 +706,7 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, k + " must be 0 or 1");
         (k == "blocked" ? c->blocked : c->fine_phases) = iv;
     } else if (k == "tile_shape") {
-        if (!integral || iv < -1 || iv > 3) return fail(LC_ERR_ARG, "tile_shape must be -1 (auto) or 0..3");
+        if (!integral || iv < -1 || iv > 4) return fail(LC_ERR_ARG, "tile_shape must be -1 (auto) or 0..4");
         c->tile_force = iv;
     } else if (k == "coarse_max") {
         if (!integral || iv < 2 || iv > 256) return fail(LC_ERR_ARG, "coarse_max must be 2..256");

@@ -254,7 +254,8 @@ void fill_tables(lc_batch *b) {
             int n = b->N[c] >> l;
             int gx = (n - 1 + tile_tx(sh) - 1) / tile_tx(sh), gy = (n - 1 + tile_ty(sh) - 1) / tile_ty(sh);
             r.gx[c] = gx;
-            if (l < b->lc[c]) s += gx * gy;
+            // shape 4: blocks of four warp tiles; otherwise one tile per block
+            if (l < b->lc[c]) s += sh == 4 ? warp_tile_blocks(n) : gx * gy;
         }
         r.start[C] = s;
         b->rblocks[1 + l] = s;
@@ -718,7 +719,7 @@ int lc_batch_autotune(lc_batch *b, int reps, int *shapes_out, int max_levels) {
     for (int l = 0; l < b->Lmax; ++l) {
         float best = 1e30f;
         int pick = -1;
-        for (int sh = 0; sh < 4; ++sh) {
+        for (int sh = 0; sh < 5; ++sh) {
             if (tile_smem_bytes(sh, b->op, nu, 4) > kMaxSmem - 1024) continue;
             b->shape[l] = sh;
             fill_tables(b);

@@ -76,6 +76,14 @@ struct FinishArgs {
 };
 
 #ifdef __CUDACC__
+// Rounded products and sums that the compiler may not fuse into an FMA: the
+// prolongation's e = w (a + b) and psi += e are written with these in every
+// kernel, so that all kernels round them alike.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 __device__ __forceinline__ double finish_block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int t = threadIdx.y * blockDim.x + threadIdx.x;
@@ -186,9 +194,11 @@ struct Correct64 {
 };
 
 // ---- shared-memory multigrid kernels (lc_mg.cu)
-// Tile shapes of the shared-memory kernels (owned nodes): 0 = 110x54,
-// 1 = 110x22, 2 = 46x22, 3 = 16x16.  tile_shape_for picks one per level
-// (force >= 0 overrides).
+// Tile shapes (owned nodes): shared-memory tiles 0 = 110x54, 1 = 110x22,
+// 2 = 46x22, 3 = 16x16; 4 = 44x20 register tiles, one per warp (lc_warp.cu;
+// FP32 only, nu <= 2 for the compact operator, so tile_smem_bytes reports it
+// as not fitting otherwise).  tile_shape_for picks one per level (force >= 0
+// overrides when the shape fits).
 int tile_shape_for(int N, int op, int nu, int elem, int force);
 int tile_tx(int shape);
 int tile_ty(int shape);
@@ -207,6 +217,15 @@ cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T
 
 constexpr size_t kMaxSmem = 227 * 1024;
 cudaError_t init_mg_kernel_attributes();
+
+// ---- register-tile (warp tile) FP32 multigrid kernels (lc_warp.cu)
+bool warp_tile_fits(int op, int nu);
+int warp_tile_blocks(int N);  // blocks of 4 warp tiles for one level of N intervals
+cudaError_t launch_down_warp(cudaStream_t s, int op, const float *g, float *e_out, int N, int P, float *gc, int Pc,
+                             int nu, float beta);
+cudaError_t launch_up_warp(cudaStream_t s, int op, const float *e_in, const float *g, const float *ec, int Pc,
+                           float *e_out, int N, int P, int nu, float beta, Correct64 cor);
+
 
 // ---- mixed-precision kernels (lc_mixed.cu)
 cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
@@ -293,6 +312,10 @@ cudaError_t launch_up_batch(cudaStream_t s, int shape, int op, BatchCav *cav, co
                             int nblocks, int nu, T beta);
 cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count, int smem, int nu1, int nu2, int nuc,
                                 float beta);
+cudaError_t launch_down_warp_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int level, int nblocks,
+                                   int nu, float beta);
+cudaError_t launch_up_warp_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int level, int nblocks,
+                                 int nu, float beta);
 cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
                                int advect, int rhs64);
 cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,

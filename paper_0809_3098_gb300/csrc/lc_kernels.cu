@@ -12,6 +12,8 @@
 // equivariant under x -> 1 - x with (psi, omega, U) -> (-psi, -omega, -U).
 #include "lc_internal.h"
 
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 namespace lcx {
@@ -189,12 +191,13 @@ __global__ void __launch_bounds__(kBX *kBY)
     if (!(i & 1) && !(j & 1))
         e = ec[cc];
     else if (i & 1 && !(j & 1))
-        e = T(0.5) * (ec[cc] + ec[cc + 1]);
+        e = mul_rn(T(0.5), ec[cc] + ec[cc + 1]);
     else if (!(i & 1) && (j & 1))
-        e = T(0.5) * (ec[cc] + ec[cc + Pc]);
+        e = mul_rn(T(0.5), ec[cc] + ec[cc + Pc]);
     else
-        e = T(0.25) * ((ec[cc] + ec[cc + 1]) + (ec[cc + Pc] + ec[cc + Pc + 1]));
-    psi[(size_t)j * Pf + i] += e;
+        e = mul_rn(T(0.25), (ec[cc] + ec[cc + 1]) + (ec[cc + Pc] + ec[cc + Pc + 1]));
+    size_t c = (size_t)j * Pf + i;
+    psi[c] = add_rn(psi[c], e);
 }
 
 // Coarsest grid (2, 3, 5 or 7 intervals: at most 36 unknowns, one thread each
@@ -532,9 +535,9 @@ cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P) {
 // fronts behind sweep k (D = 4 compact, 2 5-point: one more than the
 // stencil's reach in t), so nsw sweeps run as one pipelined pass of
 // (number of fronts) + D (nsw - 1) steps, one barrier per step.  The method
-// is sequential beyond a front, so one block does the pass; psi is updated in
-// place, in shared memory when the grid fits (SMEM) and in global memory
-// otherwise.  The node update is the smoother's expression.
+// is sequential beyond a front, so one block does the pass when the grid fits
+// its shared memory (psi updated in place there); larger grids use the
+// cluster form below.  The node update is the smoother's expression.
 template <int OP>
 __device__ __forceinline__ double sor_value(const double *p, const double *__restrict__ g, size_t c, int P) {
     double n4 = (p[c + 1] + p[c - 1]) + (p[c + P] + p[c - P]);
@@ -545,16 +548,14 @@ __device__ __forceinline__ double sor_value(const double *p, const double *__res
     return fma(0.25, n4, g[c]);
 }
 
-template <int OP, bool SMEM>
+template <int OP>
 __global__ void __launch_bounds__(1024)
     k_sor_lex(double *psi, const double *__restrict__ g, int N, int P, int nsw, double beta) {
     extern __shared__ double sor_sp[];
-    double *p = SMEM ? sor_sp : psi;
+    double *p = sor_sp;
     const size_t nodes = (size_t)(N + 1) * P;
-    if (SMEM) {
-        for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) p[q] = psi[q];
-        __syncthreads();
-    }
+    for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) p[q] = psi[q];
+    __syncthreads();
     constexpr int W = OP == 1 ? 2 : 1, D = OP == 1 ? 4 : 2;
     const int t0 = W + 1, t1 = (W + 1) * (N - 1);
     const int maxc = (N - 2) / W + 1;  // most nodes on one front
@@ -575,33 +576,102 @@ __global__ void __launch_bounds__(1024)
         }
         __syncthreads();
     }
-    if (SMEM)
-        for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) psi[q] = p[q];
+    for (size_t q = threadIdx.x; q < nodes; q += blockDim.x) psi[q] = p[q];
+}
+
+// Cluster form of the same pass for grids that do not fit one block's shared
+// memory: the kSorCluster blocks of one thread-block cluster (co-scheduled on
+// kSorCluster SMs, so the FP64 work of a step is spread over that many SMs)
+// share each step's nodes, with a cluster barrier (release / acquire at
+// cluster scope) between steps.  psi stays in global memory and is read and
+// written through L2 (ld/st.global.cg), so no block sees a stale L1 copy of a
+// node another block wrote.
+constexpr int kSorCluster = 8;
+// Dynamic shared memory requested (and not used) by each block of the
+// cluster: more than half an SM's, so that no two blocks share an SM's FP64
+// pipe.
+constexpr int kSorClusterSmem = 120 * 1024;
+
+template <int OP>
+__device__ __forceinline__ double sor_value_l2(const double *p, const double *__restrict__ g, size_t c, int P) {
+    double n4 = (__ldcg(p + c + 1) + __ldcg(p + c - 1)) + (__ldcg(p + c + P) + __ldcg(p + c - P));
+    if (OP == 1) {
+        double d4 = (__ldcg(p + c + P + 1) + __ldcg(p + c - P + 1)) + (__ldcg(p + c + P - 1) + __ldcg(p + c - P - 1));
+        return fma(0.2, n4, fma(0.05, d4, g[c]));
+    }
+    return fma(0.25, n4, g[c]);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(1024)
+    k_sor_lex_cluster(double *psi, const double *__restrict__ g, int N, int P, int nsw, double beta) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int nthreads = kSorCluster * (int)blockDim.x;
+    const int tid = (int)cl.block_rank() * (int)blockDim.x + (int)threadIdx.x;
+    constexpr int W = OP == 1 ? 2 : 1, D = OP == 1 ? 4 : 2;
+    const int t0 = W + 1, t1 = (W + 1) * (N - 1);
+    const int maxc = (N - 2) / W + 1;
+    const int steps = (t1 - t0 + 1) + D * (nsw - 1);
+    for (int s = 0; s < steps; ++s) {
+        for (int q = tid; q < nsw * maxc; q += nthreads) {
+            int k = q / maxc, r = q - k * maxc;
+            int t = t0 + s - D * k;
+            if (t < t0 || t > t1) continue;
+            int lo = t - (N - 1) > 0 ? (t - (N - 1) + W - 1) / W : 1;
+            if (lo < 1) lo = 1;
+            int i = lo + r, j = t - W * i;
+            if (i > N - 1 || j < 1) continue;
+            size_t c = (size_t)j * P + i;
+            double v = sor_value_l2<OP>(psi, g, c, P);
+            if (beta != 1.0) {
+                double o = __ldcg(psi + c);
+                v = fma(beta, v - o, o);
+            }
+            __stcg(psi + c, v);
+        }
+        cl.sync();
+    }
+}
+
+template <int OP>
+cudaError_t launch_sor_cluster(cudaStream_t s, double *psi, const double *g, int N, int P, int nsw, double beta) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kSorCluster);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = kSorClusterSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kSorCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_sor_lex_cluster<OP>, psi, g, N, P, nsw, beta);
 }
 
 size_t sor_smem_bytes(int N, int P) { return (size_t)(N + 1) * P * sizeof(double); }
 
 cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g, int N, int P, int nsw, double beta) {
     size_t sm = sor_smem_bytes(N, P);
-    bool fits = sm <= (size_t)kMaxSmem;
-    if (op == 1) {
-        if (fits)
-            k_sor_lex<1, true><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
-        else
-            k_sor_lex<1, false><<<1, 1024, 0, s>>>(psi, g, N, P, nsw, beta);
-    } else {
-        if (fits)
-            k_sor_lex<0, true><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
-        else
-            k_sor_lex<0, false><<<1, 1024, 0, s>>>(psi, g, N, P, nsw, beta);
-    }
+    if (sm > (size_t)kMaxSmem)
+        return op == 1 ? launch_sor_cluster<1>(s, psi, g, N, P, nsw, beta)
+                       : launch_sor_cluster<0>(s, psi, g, N, P, nsw, beta);
+    if (op == 1)
+        k_sor_lex<1><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
+    else
+        k_sor_lex<0><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
     return cudaGetLastError();
 }
 
 cudaError_t init_sor_kernel_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(k_sor_lex<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_sor_lex<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_sor_lex<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sor_lex<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem);
+        e = cudaFuncSetAttribute(k_sor_lex_cluster<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSorClusterSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_sor_lex_cluster<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSorClusterSmem);
     return e;
 }
 

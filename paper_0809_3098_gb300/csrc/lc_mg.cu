@@ -333,12 +333,12 @@ __device__ __forceinline__ double up_body(int bx, int by, const T *__restrict__ 
             if (!(gi & 1) && !(gj & 1))
                 e = sc[cc];
             else if ((gi & 1) && !(gj & 1))
-                e = T(0.5) * (sc[cc] + sc[cc + 1]);
+                e = mul_rn(T(0.5), sc[cc] + sc[cc + 1]);
             else if (!(gi & 1) && (gj & 1))
-                e = T(0.5) * (sc[cc] + sc[cc + LXc]);
+                e = mul_rn(T(0.5), sc[cc] + sc[cc + LXc]);
             else
-                e = T(0.25) * ((sc[cc] + sc[cc + 1]) + (sc[cc + LXc] + sc[cc + LXc + 1]));
-            sp[y * LP + x] += e;
+                e = mul_rn(T(0.25), (sc[cc] + sc[cc + 1]) + (sc[cc + LXc] + sc[cc + LXc + 1]));
+            sp[y * LP + x] = add_rn(sp[y * LP + x], e);
         }
     }
     __syncthreads();
@@ -481,12 +481,12 @@ __device__ __forceinline__ double coarse_body(const T *__restrict__ g_in, int Pg
                 if (!(i & 1) && !(j & 1))
                     e = ec[cc];
                 else if ((i & 1) && !(j & 1))
-                    e = T(0.5) * (ec[cc] + ec[cc + 1]);
+                    e = mul_rn(T(0.5), ec[cc] + ec[cc + 1]);
                 else if (!(i & 1) && (j & 1))
-                    e = T(0.5) * (ec[cc] + ec[cc + LPc]);
+                    e = mul_rn(T(0.5), ec[cc] + ec[cc + LPc]);
                 else
-                    e = T(0.25) * ((ec[cc] + ec[cc + 1]) + (ec[cc + LPc] + ec[cc + LPc + 1]));
-                sp[j * LP + i] += e;
+                    e = mul_rn(T(0.25), (ec[cc] + ec[cc + 1]) + (ec[cc + LPc] + ec[cc + LPc + 1]));
+                sp[j * LP + i] = add_rn(sp[j * LP + i], e);
             }
         __syncthreads();
         cs_sweeps<T, OP>(sp, sg, n, nu2, beta);
@@ -591,8 +591,9 @@ __global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, i
                            beta, false, smem_raw);
 }
 
-constexpr int kShapeTX[4] = {110, 110, 46, 16};
-constexpr int kShapeTY[4] = {54, 22, 22, 16};
+constexpr int kShapeTX[5] = {110, 110, 46, 16, 44};
+constexpr int kShapeTY[5] = {54, 22, 22, 16, 20};
+constexpr int kShapes = 5;
 
 }  // namespace
 
@@ -604,6 +605,7 @@ int tiles_of(int N, int shape) {
 }
 
 size_t tile_smem_bytes(int shape, int op, int nu, int elem) {
+    if (shape == 4) return elem == 4 && warp_tile_fits(op, nu) ? 0 : ~size_t(0) / 2;  // registers only
     int LX = tile_lx(kShapeTX[shape], op, nu), LY = tile_ly(kShapeTY[shape], nu), LP = tile_lp(LX);
     return (2 * (size_t)LY * LP + (size_t)tile_lxc(LX) * tile_lxc(LY)) * elem;
 }
@@ -614,7 +616,10 @@ size_t tile_smem_bytes(int shape, int op, int nu, int elem) {
 // halo); FP32 tiles are latency-bound, so a launch costs (waves of resident
 // blocks) x (a fixed barrier-chain latency + a small per-node term).
 int tile_shape_for(int N, int op, int nu, int elem, int force) {
-    if (force >= 0 && force < 4 && tile_smem_bytes(force, op, nu, elem) <= kMaxSmem - 1024) return force;
+    if (force >= 0 && force < kShapes && tile_smem_bytes(force, op, nu, elem) <= kMaxSmem - 1024) return force;
+    // The register tiles (shape 4) are only taken when forced or measured
+    // faster by the batch autotuner: at 206-238 registers per thread they keep
+    // 8 warps per SM, too few to hide their global loads.
     const int sms = 152;
     double best = 1e300;
     int pick = 3;
@@ -643,6 +648,11 @@ namespace {
 template <typename T, int OP>
 cudaError_t down_shape(cudaStream_t s, int shape, const T *psi_in, int zero_init, const T *g, T *psi_out, int N, int P,
                        T *gc, int Pc, int nu, T beta) {
+    if (shape == 4) {  // FP32 register tiles, zero initial correction only
+        if (sizeof(T) != 4 || !zero_init) return cudaErrorInvalidValue;
+        return launch_down_warp(s, OP, reinterpret_cast<const float *>(g), reinterpret_cast<float *>(psi_out), N, P,
+                                reinterpret_cast<float *>(gc), Pc, nu, (float)beta);
+    }
     switch (shape) {
         case 0: return down_t<T, OP, 110, 54>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
         case 1: return down_t<T, OP, 110, 22>(s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
@@ -654,6 +664,12 @@ cudaError_t down_shape(cudaStream_t s, int shape, const T *psi_in, int zero_init
 template <typename T, int OP>
 cudaError_t up_shape(cudaStream_t s, int shape, const T *psi_in, const T *g, const T *ec, int Pc, T *psi_out, int N,
                      int P, int nu, T beta, double *partials, Correct64 cor, FinishArgs fin) {
+    if (shape == 4) {  // FP32 register tiles; no residual norm
+        if (sizeof(T) != 4 || partials || fin.enabled) return cudaErrorInvalidValue;
+        return launch_up_warp(s, OP, reinterpret_cast<const float *>(psi_in), reinterpret_cast<const float *>(g),
+                              reinterpret_cast<const float *>(ec), Pc, reinterpret_cast<float *>(psi_out), N, P, nu,
+                              (float)beta, cor);
+    }
     switch (shape) {
         case 0: return up_t<T, OP, 110, 54>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
         case 1: return up_t<T, OP, 110, 22>(s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
@@ -740,6 +756,7 @@ cudaError_t up_batch_shape(cudaStream_t s, int shape, BatchCav *cav, const Batch
 template <>
 cudaError_t launch_down_batch<float>(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
                                      int nblocks, int nu, float beta) {
+    if (shape == 4) return launch_down_warp_batch(s, op, cav, r, level, nblocks, nu, beta);
     return op == 1 ? down_batch_shape<1>(s, shape, cav, r, level, nblocks, nu, beta)
                    : down_batch_shape<0>(s, shape, cav, r, level, nblocks, nu, beta);
 }
@@ -747,6 +764,7 @@ cudaError_t launch_down_batch<float>(cudaStream_t s, int shape, int op, BatchCav
 template <>
 cudaError_t launch_up_batch<float>(cudaStream_t s, int shape, int op, BatchCav *cav, const BatchRange *r, int level,
                                    int nblocks, int nu, float beta) {
+    if (shape == 4) return launch_up_warp_batch(s, op, cav, r, level, nblocks, nu, beta);
     return op == 1 ? up_batch_shape<1>(s, shape, cav, r, level, nblocks, nu, beta)
                    : up_batch_shape<0>(s, shape, cav, r, level, nblocks, nu, beta);
 }

@@ -115,11 +115,16 @@ def test_mixed_errors_reported():
     assert e.value.code == lc.LC_ERR_NOCONV
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3])
-def test_mixed_tile_shapes_bitwise_identical(shape):
-    N = 384
-    a = lc.Cavity(N, 5000.0, precision=MIXED, tile_shape=shape)
-    b = lc.Cavity(N, 5000.0, precision=MIXED, tile_shape=2)
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("N,op,nu", [(384, lc.LC_OP_COMPACT, 2), (320, lc.LC_OP_COMPACT, 1),
+                                     (224, lc.LC_OP_5PT, 2), (256, lc.LC_OP_COMPACT, 3)])
+def test_mixed_tile_shapes_bitwise_identical(shape, N, op, nu):
+    """Shared-memory tiles (0-3) and the warp register tiles (4; they need
+    nu <= 2 with the compact operator, else the default shape runs) give the
+    same bits: each recomputes a halo wide enough for the owned nodes."""
+    a = lc.Cavity(N, 5000.0, precision=MIXED, op=op, nu1=nu, nu2=nu, tile_shape=shape)
+    b = lc.Cavity(N, 5000.0, precision=MIXED, op=op, nu1=nu, nu2=nu, tile_shape=2)
     a.step(2)
     b.step(2)
+    assert np.array_equal(a.cycle_log(), b.cycle_log())
     assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
