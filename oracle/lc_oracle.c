@@ -315,8 +315,8 @@ static int mg_init(or_mg *mg, int N, int op) {
     if (nlev < 1 || nlev > OR_MAX_LEVELS) return OR_ERR_ARG;
     mg->op = op;
     mg->nlev = nlev;
-    mg->nu1 = 2;
-    mg->nu2 = 2;
+    mg->nu1 = 2; /* V(2,1), the library's default: the paper fixes no */
+    mg->nu2 = 1; /* smoothing counts (reading R7)                      */
     mg->nuc = 16;
     mg->solver = OR_SOLVER_MG;
     mg->sor_sweeps = 16;
