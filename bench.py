@@ -47,6 +47,9 @@ from paper_0809_3098_gb300.workloads import CAVITY_128_RE1000, CAVITY_1024_RE100
 # fp64-4096 is a profiling case: its fields (134 MB each) exceed the 126 MB L2.
 WORKLOADS = {"fp64-1024": CAVITY_1024_RE10000, "fp64-128": CAVITY_128_RE1000,
              "fp64-4096": Workload("cavity-4096-Re10000-fp64", 4096, 10000.0, 10)}
+# Multigrid smoothing schedule V(nu1, nu2) of the single-cavity runs (the
+# library's default, set explicitly so that the kernel counts below match).
+SCHEDULE = {"nu1": 2, "nu2": 1}
 METRIC = "grid-point-stage updates/s"
 UNIT = "updates/s"
 L2_FLUSH_BYTES = 256 << 20
@@ -140,7 +143,7 @@ def cpu_oracle_rate(wl: Workload, budget_s: float):
     least one step and until budget_s has passed.  Returns (updates/s, steps, s)."""
     import oracle
 
-    cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol)
+    cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **SCHEDULE)
     steps, t0 = 0, time.perf_counter()
     while True:
         cav.step(1)
@@ -158,7 +161,7 @@ def run_reference(args, wl: Workload):
         return 0
     import oracle
 
-    cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol)
+    cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **SCHEDULE)
     cav.step(args.warmup)
     t0 = time.perf_counter()
     cav.step(args.steps)
@@ -181,7 +184,8 @@ def run_reference(args, wl: Workload):
 def config_of(wl: Workload, gpus: int, precision: str = "fp64") -> dict:
     name = wl.name if precision == "fp64" else wl.name.replace("-fp64", "-mixed")
     return {"workload": name, "N": wl.N, "Re": wl.Re, "dt": wl.dt, "tol": wl.tol, "op": wl.op,
-            "precision": precision, "start": "rest (psi = omega = 0)",
+            "precision": precision, "schedule": f"V({SCHEDULE['nu1']},{SCHEDULE['nu2']})",
+            "start": "rest (psi = omega = 0)",
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": "replicas" if gpus > 1 else "single"}
 
@@ -218,7 +222,7 @@ def job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
 # Kernels lc_bench_kernel can time, and how many times each runs per step
 # (c = V-cycles in the step's five solves).
 KERNELS = {
-    "fp64": [("k_smooth_colour<double,compact> (fine level, one colour phase)", lambda c, nu: 4 * 2 * nu * c),
+    "fp64": [("k_smooth_colour<double,compact> (fine level, one colour phase)", lambda c, nu: 4 * nu * c),
              ("k_rhs_stage (fused L(omega) + stage combination)", lambda c, nu: 5),
              ("k_residual_restrict<double,compact> (fine level)", lambda c, nu: c)],
     "mixed": [("k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)", lambda c, nu: c),
@@ -239,7 +243,7 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
     rows = []
     for kid, (name, count) in enumerate(KERNELS[precision]):
         ms, nbytes, f64, f32 = lc.lc_bench_kernel(cav.handle, kid, 100)
-        share_ms = ms * count(cycles_per_step, 2)
+        share_ms = ms * count(cycles_per_step, SCHEDULE["nu1"] + SCHEDULE["nu2"])
         fr = {"hbm": nbytes / (ms * 1e-3) / 1e9 / hbm, "alu64": f64 / (ms * 1e-3) / 1e12 / p64,
               "alu32": f32 / (ms * 1e-3) / 1e12 / p32}
         rows.append((share_ms, kid, name, ms, nbytes, f64, f32, fr))
@@ -259,7 +263,7 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
     roof["traffic"] = None
     roof["kernel"] = name
     roof["kernel_ms"] = ms
-    roof["launches_per_step"] = KERNELS[precision][kid][1](cycles_per_step, 2)
+    roof["launches_per_step"] = KERNELS[precision][kid][1](cycles_per_step, SCHEDULE["nu1"] + SCHEDULE["nu2"])
     roof["algorithmic_bytes"] = nbytes
     roof["fp64_flops"] = f64
     roof["fp32_flops"] = f32
@@ -272,7 +276,8 @@ def timed_run(lc, torch, dist, wl: Workload, precision: str, steps: int, warmup:
               sample_clocks: int | None):
     """W warm-up steps, then K steps each bracketed by CUDA events on the
     context's stream, with an L2 flush between them."""
-    opts = {"op": lc.LC_OP_COMPACT, "precision": lc.LC_PREC_MIXED if precision == "mixed" else lc.LC_PREC_FP64}
+    opts = {"op": lc.LC_OP_COMPACT, "precision": lc.LC_PREC_MIXED if precision == "mixed" else lc.LC_PREC_FP64,
+            **SCHEDULE}
     if eager:
         opts["graph"] = 0
     cav = lc.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **opts)

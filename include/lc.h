@@ -109,7 +109,7 @@ const char *lc_last_error(void);
 /* Sets an option; value is converted to the option's type.  Keys:
  *   "op"          LC_OP_5PT or LC_OP_COMPACT (default)       [before first use]
  *   "precision"   LC_PREC_FP64 (default) or LC_PREC_MIXED   [before first use]
- *   "nu1","nu2"   pre/post smoothing sweeps per level (2, 2), 1..16
+ *   "nu1","nu2"   pre/post smoothing sweeps per level (2, 1), 1..16
  *   "nuc"         sweeps on the coarsest grid (16), 1..256
  *   "beta"        relaxation of the SOR update, Eq. (15) (1.0), 0 < beta < 2
  *   "max_cycles"  cycle cap per solve (100); hitting it raises LC_ERR_NOCONV

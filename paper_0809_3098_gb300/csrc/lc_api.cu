@@ -148,7 +148,7 @@ struct lc_ctx {
     int N;
     double Re, dt, tol;
     int op = LC_OP_COMPACT, precision = LC_PREC_FP64;
-    int nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
+    int nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
     int use_graph = 1;
     double beta = 1.0, U = 1.0;
     int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR

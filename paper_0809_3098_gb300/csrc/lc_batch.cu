@@ -72,7 +72,7 @@ struct lc_batch {
     std::vector<int> N, nlev, lc;
     std::vector<double> Re, dt;
     double tol = 1e-10, beta = 1.0, U = 1.0;
-    int op = LC_OP_COMPACT, nu1 = 2, nu2 = 2, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
+    int op = LC_OP_COMPACT, nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
     int use_graph = 1, rhs64 = 0;
     int Lmax = 0;
     std::vector<int> shape;  // tile shape per level (< Lmax)
@@ -219,6 +219,10 @@ void fill_tables(lc_batch *b) {
         }
         v.Re = b->Re[c];
         v.dt = b->dt[c];
+        double h = 1.0 / v.N;
+        v.h2 = h * h;
+        v.nu_invh2 = (double)v.N * (double)v.N / v.Re;
+        v.nu_invh2f = (float)((double)v.N * (double)v.N / v.Re);
         v.psi64 = b->at<double>(L.psi64[c]);
         v.g64 = b->at<double>(L.g64[c]);
         v.psi32 = b->at<float>(L.psi32[c]);

@@ -255,6 +255,11 @@ struct BatchCav {
     double *W[4];  // W0, Wa, Wb, ACC
     float *Ws[3];  // FP32 shadows of W0, Wa, Wb
     int *log;      // cycles per solve, ring of kLogN
+    // per-cavity constants, computed on the host as the single-cavity
+    // launchers compute them (no division in the kernels)
+    double h2, nu_invh2;  // h^2 and N^2 / Re
+    float nu_invh2f;      // (float)(N^2 / Re)
+    int pad0;
     // solve state
     int active, cycles, status, last_cycles;
     unsigned int arrive;

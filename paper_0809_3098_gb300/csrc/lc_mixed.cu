@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     double Ld, wPd = in64[c];
     if (RHS64) {
         const double *psi = cv.psi64;
-        double inv2h = 0.5 * N, nu_invh2 = (double)N * (double)N / cv.Re;
+        double inv2h = 0.5 * N, nu_invh2 = cv.nu_invh2;
         double wE = in64[c + 1], wW = in64[c - 1], wN = in64[c + P], wS = in64[c - P];
         Ld = nu_invh2 * fma(-4.0, wPd, (wE + wW) + (wN + wS));
         if (advect) {
@@ -234,8 +234,8 @@ __global__ void __launch_bounds__(kBX *kBY)
         }
     } else {
         const float *in32 = cv.Ws[stage_in(stage)], *psi = cv.psi32;
-        float inv2h = (float)(0.5 * N);
-        float nu_invh2 = (float)((double)N * (double)N / cv.Re);
+        float inv2h = 0.5f * (float)N;  // exact: the value (float)(0.5 N) of the single-cavity launcher
+        float nu_invh2 = cv.nu_invh2f;
         float wP = in32[c], wE = in32[c + 1], wW = in32[c - 1], wN = in32[c + P], wS = in32[c - P];
         float L = nu_invh2 * fmaf(-4.0f, wP, (wE + wW) + (wN + wS));
         if (advect) {
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     if (bx == 0 && by == 0 && threadIdx.x == 0 && threadIdx.y == 0) cv.active = 1;
     int N = cv.N, P = cv.P[0];
     const double *w = cv.W[stage_out(stage)];
-    double h2 = (1.0 / N) * (1.0 / N);
+    double h2 = cv.h2;
     int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
     double v = 0.0;
     if (i < N && j < N) {

@@ -41,7 +41,7 @@ def test_batch_eager_equals_graph_and_autotune_keeps_bits():
     e.step(2)
     t.step(1)
     shapes = t.autotune(reps=2)
-    assert len(shapes) >= 1 and all(0 <= s <= 3 for s in shapes)
+    assert len(shapes) >= 1 and all(0 <= s <= 4 for s in shapes)
     t.step(1)
     for c in range(3):
         assert np.array_equal(a.psi(c), e.psi(c)) and np.array_equal(a.omega(c), e.omega(c))
