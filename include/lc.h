@@ -268,8 +268,9 @@ int lc_batch_synchronize(lc_batch *b);
 int lc_batch_info(lc_batch *b, int cavity, double out[8]);
 
 /* Autotuner: for every tile level, times `reps` launches of the batch's
- * pre- and post-smoothing tile kernels in each tile shape (110x54, 110x22,
- * 46x22, 16x16 owned nodes; those that fit in shared memory) on the current
+ * pre- and post-smoothing tile kernels in each tile shape (0..3: shared-
+ * memory tiles of 110x54, 110x22, 46x22, 16x16 owned nodes, those that fit;
+ * 4: 44x20 register tiles, one per warp, where the halo fits) on the current
  * state, keeps the fastest, and writes the chosen shape per level to
  * shapes_out[0..max_levels) (-1 past the last tile level).  The tile shape
  * does not change any result (bit-identical); the state is restored. */

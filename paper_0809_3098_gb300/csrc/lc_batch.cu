@@ -57,6 +57,7 @@ int nlevels(int N) {
 }
 
 constexpr int kSBX = 32, kSBY = 8;  // stage-kernel block
+constexpr int kResRange = 1 + kMaxLevels;  // index of the residual kernels' block range
 
 struct BLayout {
     std::vector<size_t> psi64, g64, psi32, W[4], Ws[3], log;
@@ -178,14 +179,17 @@ bool plan(lc_batch *b) {
         size_t cs = coarse_smem_bytes(N >> cl, b->nlev[c] - cl, 4);
         if (cs > b->coarse_smem) b->coarse_smem = cs;
     }
-    L.nranges = 1 + b->Lmax;
+    L.nranges = 2 + kMaxLevels;  // [0] stage, [1 + l] level-l tiles, [kResRange] residual
     L.cav = take(sizeof(BatchCav) * C);
-    L.ranges = take(sizeof(BatchRange) * (1 + kMaxLevels));  // independent of the options
+    L.ranges = take(sizeof(BatchRange) * L.nranges);  // independent of the options
     L.state = take(sizeof(BatchState));
-    int sb = 0;
-    for (int c = 0; c < C; ++c) sb += stage_blocks_of(b->N[c]);
+    int sb = 0, rb = 0;
+    for (int c = 0; c < C; ++c) {
+        sb += stage_blocks_of(b->N[c]);
+        rb += residual_norm_blocks(b->N[c]);
+    }
     L.stage_blocks = sb;
-    L.rpart = take(sizeof(double) * sb);
+    L.rpart = take(sizeof(double) * rb);
     L.gpart = take(sizeof(double) * sb);
     L.total = off;
     return true;
@@ -244,6 +248,19 @@ void fill_tables(lc_batch *b) {
         }
         r.start[C] = s;
         b->rblocks[0] = s;
+    }
+    // residual range: every cavity, blocks of kRX x kRY interior nodes
+    {
+        BatchRange &r = b->hr[kResRange];
+        r.count = C;
+        int s = 0;
+        for (int c = 0; c < C; ++c) {
+            r.start[c] = s;
+            r.gx[c] = residual_blocks_x(b->N[c]);
+            s += residual_norm_blocks(b->N[c]);
+        }
+        r.start[C] = s;
+        b->rblocks[kResRange] = s;
     }
     // level-l tile ranges: cavities whose level l is a tile level (l < lc).
     // Cavities are listed in order; a cavity without level-l tiles gets an
@@ -313,7 +330,8 @@ int enqueue_cycle(lc_batch *b, cudaStream_t s, cudaGraphConditionalHandle h) {
             LB_CUDA(launch_up_batch<float>(s, shape_of(b, l), b->op, b->dcav(), b->drange(1 + l), l,
                                            b->rblocks[1 + l], b->nu2, beta));
     BatchFinish fin{1, b->tol, b->max_cycles, h, b->dstate()};
-    LB_CUDA(launch_residual_batch(s, b->op, b->dcav(), b->drange(0), b->rblocks[0], b->at<double>(b->lay.rpart),
+    LB_CUDA(launch_residual_batch(s, b->op, b->dcav(), b->drange(kResRange), b->drange(0), b->rblocks[kResRange],
+                                  b->at<double>(b->lay.rpart),
                                   b->at<double>(b->lay.gpart), fin));
     return LC_OK;
 }
@@ -323,7 +341,8 @@ int enqueue_head(lc_batch *b, cudaStream_t s, int stage) {
     LB_CUDA(launch_assemble_batch(s, b->op, b->dcav(), b->drange(0), b->rblocks[0], stage,
                                   b->at<double>(b->lay.gpart)));
     BatchFinish none{0, 0.0, 0, 0, nullptr};
-    LB_CUDA(launch_residual_batch(s, b->op, b->dcav(), b->drange(0), b->rblocks[0], b->at<double>(b->lay.rpart),
+    LB_CUDA(launch_residual_batch(s, b->op, b->dcav(), b->drange(kResRange), b->drange(0), b->rblocks[kResRange],
+                                  b->at<double>(b->lay.rpart),
                                   b->at<double>(b->lay.gpart), none));
     return LC_OK;
 }

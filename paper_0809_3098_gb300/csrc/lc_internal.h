@@ -84,6 +84,41 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
+// Scaled residual rho = (Gauss-Seidel value) - psi of node (i, j),
+// i = i0 - 1 + lane, for a warp over 32 consecutive columns of row j >= 1
+// (blockDim.x = 32); lanes 0 and 31 are halo and only supply column data.
+// Compact operator: with the column sums V(k) = psi(k, j+1) + psi(k, j-1) and
+// H(k) = 4 psi(k, j) + V(k),
+//   GS = 0.2 n4 + 0.05 d4 + g = 0.05 (H(i+1) + H(i-1) + 4 V(i)) + g,
+// six FP64 operations per node instead of seven, mirror-image terms still
+// paired; H(i +- 1) come from the neighbouring lanes.  5-point: 0.25 n4 + g
+// with n4 = (E + W) + V(i).  Returns whether (i, j) is an interior node.
+template <typename T, int OP>
+__device__ __forceinline__ bool rho_halo(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, int i0,
+                                         int j, T &rho) {
+    int lane = threadIdx.x & 31;
+    int i = i0 - 1 + lane;
+    bool rowok = j < N;
+    size_t c = (size_t)j * P + i;
+    T p = T(0), V = T(0);
+    if (rowok && i <= N) {
+        p = psi[c];
+        V = psi[c + P] + psi[c - P];
+    }
+    bool act = rowok && lane >= 1 && lane <= 30 && i < N;
+    if (OP == 1) {
+        T H = fma(T(4), p, V);
+        T Hr = __shfl_down_sync(0xffffffffu, H, 1), Hl = __shfl_up_sync(0xffffffffu, H, 1);
+        if (!act) return false;
+        rho = fma(T(0.05), fma(T(4), V, Hr + Hl), g[c] - p);
+    } else {
+        T E = __shfl_down_sync(0xffffffffu, p, 1), W = __shfl_up_sync(0xffffffffu, p, 1);
+        if (!act) return false;
+        rho = fma(T(0.25), (E + W) + V, g[c]) - p;
+    }
+    return true;
+}
+
 __device__ __forceinline__ double finish_block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int t = threadIdx.y * blockDim.x + threadIdx.x;
@@ -165,6 +200,11 @@ template <typename T>
 cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials,
                                  FinishArgs fin);
 
+// Residual kernels: a warp covers 32 consecutive columns of one row, the
+// outer two lanes as halo, so a block of 32 x 8 threads owns kRX = 30 x 8
+// interior nodes.
+constexpr int kRX = 30, kRY = 8;
+inline int residual_blocks_x(int N) { return (N - 1 + kRX - 1) / kRX; }
 int residual_norm_blocks(int N);
 // nsw lexicographic SOR sweeps (Eq. (15) in its superscripts' order) in one
 // block, pipelined over wavefronts; psi in shared memory when
@@ -325,8 +365,10 @@ cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *
                                int advect, int rhs64);
 cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
                                   double *gpart);
-cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks,
-                                  double *rpart, const double *gpart, BatchFinish fin);
+// r: the residual range (blocks of kRX x kRY nodes); rg: the stage range, whose
+// blocks wrote gpart.
+cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, const BatchRange *rg,
+                                  int nblocks, double *rpart, const double *gpart, BatchFinish fin);
 cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U);
 cudaError_t launch_psi32_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks);
 cudaError_t launch_to32_batch(cudaStream_t s, BatchCav *cav, int c);

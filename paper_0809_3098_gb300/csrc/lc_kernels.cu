@@ -222,34 +222,20 @@ __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, 
         }
 }
 
-// Per-block partial sums of rho^2 over interior nodes (FP64 accumulation).
-// The column sums V(k) = psi(k, j+1) + psi(k, j-1) are formed once per column
-// and passed between neighbouring lanes (blockDim.x = 32: a warp is 32
-// consecutive columns of one row), so n4 = (E + W) + V(i) and
-// d4 = V(i+1) + V(i-1) cost 4 additions instead of 6, in gs_value's order.
+// Per-block partial sums of rho^2 over interior nodes (FP64 accumulation); a
+// block of 32 x 8 threads covers 30 x 8 interior nodes (rho_halo: the outer
+// lanes of each warp are halo).
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials,
                     FinishArgs fin) {
     __shared__ double sh[32];
-    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int i0 = 1 + blockIdx.x * kRX;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     double v = 0.0;
-    bool rowok = j < N;
-    size_t c = (size_t)j * P + i;
-    T Vc = (rowok && i <= N) ? psi[c + P] + psi[c - P] : T(0);
-    T Vr = __shfl_down_sync(0xffffffffu, Vc, 1), Vl = __shfl_up_sync(0xffffffffu, Vc, 1);
-    if (rowok && i < N) {
-        T n4 = (psi[c + 1] + psi[c - 1]) + Vc;
-        T gs;
-        if (OP == 1) {
-            if (threadIdx.x == 31) Vr = psi[c + P + 1] + psi[c - P + 1];
-            if (threadIdx.x == 0) Vl = psi[c + P - 1] + psi[c - P - 1];
-            gs = fma(T(0.2), n4, fma(T(0.05), Vr + Vl, g[c]));
-        } else {
-            gs = fma(T(0.25), n4, g[c]);
-        }
-        double r = (double)(gs - psi[c]);
+    T rho;
+    if (rho_halo<T, OP>(psi, g, N, P, i0, j, rho)) {
+        double r = (double)rho;
         v = r * r;
     }
     v = block_sum(v, sh);
@@ -419,17 +405,20 @@ inline dim3 grid2(int nx, int ny, int bx, int by) { return dim3((nx + bx - 1) / 
 // ---------------------------------------------------------------------------
 template <typename T>
 cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int colour, T beta) {
-    dim3 blk(kBX, kBY);
+    // Two-warp blocks: a phase is about one wave of work, and small blocks
+    // spread it evenly over the SMs.
+    constexpr int kSmY = 2;
+    dim3 blk(kBX, kSmY);
     bool relax = beta != T(1);
     if (op == 1) {
         int n = N / 2;                      // at most this many nodes of one parity per direction
-        dim3 grid = grid2(n, (n + 1) / 2, kBX, kBY);  // two rows per thread
+        dim3 grid = grid2(n, (n + 1) / 2, kBX, kSmY);  // two rows per thread
         if (relax)
             k_smooth_colour<T, 1, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
         else
             k_smooth_colour<T, 1, false><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
     } else {
-        dim3 grid = grid2(N / 2, N / 2, kBX, kBY);  // two rows per thread
+        dim3 grid = grid2(N / 2, N / 2, kBX, kSmY);  // two rows per thread
         if (relax)
             k_smooth_colour<T, 0, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
         else
@@ -465,14 +454,14 @@ cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, i
     return cudaGetLastError();
 }
 
-int residual_norm_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY - 1) / kBY); }
-int assemble_blocks(int N) { return residual_norm_blocks(N); }
+int residual_norm_blocks(int N) { return residual_blocks_x(N) * ((N - 1 + kRY - 1) / kRY); }
+int assemble_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY - 1) / kBY); }
 int monitor_blocks(int N) { return ((N + 1 + kBX - 1) / kBX) * ((N + 1 + kBY - 1) / kBY); }
 
 template <typename T>
 cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials,
                                  FinishArgs fin) {
-    dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
+    dim3 grid(residual_blocks_x(N), (N - 1 + kRY - 1) / kRY), blk(kBX, kRY);
     if (op == 1)
         k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
     else

@@ -35,34 +35,6 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
-// FP64 scaled residual rho = (Gauss-Seidel value) - psi at node (i, j) of a
-// warp that covers 32 consecutive columns of one row (blockDim.x = 32; every
-// lane calls this).  The column sums V(k) = psi(k, j+1) + psi(k, j-1) are
-// computed once and passed between neighbouring lanes, so that
-// n4 = (E + W) + V(i) and d4 = V(i+1) + V(i-1), in the order of every other
-// kernel.  Returns whether (i, j) is an interior node.
-template <int OP>
-__device__ __forceinline__ bool rho64_shared(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
-                                             int i, int j, double &rho) {
-    bool rowok = j < N;
-    size_t c = (size_t)j * P + i;
-    double Vc = (rowok && i <= N) ? psi[c + P] + psi[c - P] : 0.0;
-    double Vr = __shfl_down_sync(0xffffffffu, Vc, 1), Vl = __shfl_up_sync(0xffffffffu, Vc, 1);
-    bool act = rowok && i < N;
-    if (!act) return false;
-    double n4 = (psi[c + 1] + psi[c - 1]) + Vc;
-    double gs;
-    if (OP == 1) {
-        if (threadIdx.x == 31) Vr = psi[c + P + 1] + psi[c - P + 1];
-        if (threadIdx.x == 0) Vl = psi[c + P - 1] + psi[c - P - 1];
-        gs = fma(0.2, n4, fma(0.05, Vr + Vl, g[c]));
-    } else {
-        gs = fma(0.25, n4, g[c]);
-    }
-    rho = gs - psi[c];
-    return true;
-}
-
 __device__ __forceinline__ float block_sum_f(float v, float *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int t = threadIdx.y * blockDim.x + threadIdx.x;
@@ -88,13 +60,13 @@ __global__ void __launch_bounds__(kBX *kBY)
     k_residual64_to32(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
                       float *__restrict__ r32, int P32, double *__restrict__ partials, FinishArgs fin) {
     __shared__ float sh[32];
-    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    int i0 = 1 + blockIdx.x * kRX;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     float v = 0.0f;
     double rho;
-    if (rho64_shared<OP>(psi, g, N, P, i, j, rho)) {
+    if (rho_halo<double, OP>(psi, g, N, P, i0, j, rho)) {
         float r = (float)rho;
-        r32[(size_t)j * P32 + i] = r;
+        r32[(size_t)j * P32 + i0 - 1 + (int)(threadIdx.x & 31)] = r;
         v = r * r;
     }
     v = block_sum_f(v, sh);
@@ -296,8 +268,8 @@ __global__ void __launch_bounds__(kBX *kBY)
 // the loop condition: go on while any cavity iterates.
 template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
-    k_residual_batch(BatchCav *cav, const BatchRange *r, double *__restrict__ rpart, const double *__restrict__ gpart,
-                     BatchFinish fin) {
+    k_residual_batch(BatchCav *cav, const BatchRange *r, const BatchRange *rg, double *__restrict__ rpart,
+                     const double *__restrict__ gpart, BatchFinish fin) {
     __shared__ double sh[32];
     __shared__ float shf[32];
     __shared__ unsigned int s_last;
@@ -305,12 +277,12 @@ __global__ void __launch_bounds__(kBX *kBY)
     int ci = batch_locate(r, bx, by);
     BatchCav &cv = cav[ci];
     int N = cv.N, P = cv.P[0];
-    int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
+    int i0 = 1 + bx * kRX, j = 1 + by * kRY + threadIdx.y;
     float v = 0.0f;
     double rho;
-    if (cv.active && rho64_shared<OP>(cv.psi64, cv.g64, N, P, i, j, rho)) {
+    if (cv.active && rho_halo<double, OP>(cv.psi64, cv.g64, N, P, i0, j, rho)) {
         float rf = (float)rho;
-        cv.g32[0][(size_t)j * P + i] = rf;
+        cv.g32[0][(size_t)j * P + i0 - 1 + (int)(threadIdx.x & 31)] = rf;
         v = rf * rf;
     }
     v = block_sum_f(v, shf);
@@ -328,8 +300,9 @@ __global__ void __launch_bounds__(kBX *kBY)
     __threadfence();
     if (cv.active) {
         double sr = 0.0, sg = 0.0;
+        int g0 = rg->start[ci], ng = rg->start[ci + 1] - g0;
         for (int k = tid; k < nb; k += nt) sr += __ldcg(rpart + b0 + k);
-        for (int k = tid; k < nb; k += nt) sg += __ldcg(gpart + b0 + k);
+        for (int k = tid; k < ng; k += nt) sg += __ldcg(gpart + g0 + k);
         sr = block_sum(sr, sh);
         sg = block_sum(sg, sh);
         if (tid == 0) {
@@ -450,12 +423,12 @@ cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const B
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks,
-                                  double *rpart, const double *gpart, BatchFinish fin) {
+cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, const BatchRange *rg,
+                                  int nblocks, double *rpart, const double *gpart, BatchFinish fin) {
     if (op == 1)
-        k_residual_batch<1><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
+        k_residual_batch<1><<<nblocks, dim3(kBX, kRY), 0, s>>>(cav, r, rg, rpart, gpart, fin);
     else
-        k_residual_batch<0><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, rpart, gpart, fin);
+        k_residual_batch<0><<<nblocks, dim3(kBX, kRY), 0, s>>>(cav, r, rg, rpart, gpart, fin);
     return cudaGetLastError();
 }
 
@@ -472,12 +445,11 @@ cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U
 
 cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, const double *g64, int N, int P64,
                                    float *r32, int P32, double *partials, FinishArgs fin) {
+    dim3 grid(residual_blocks_x(N), (N - 1 + kRY - 1) / kRY);
     if (op == 1)
-        k_residual64_to32<1><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials,
-                                                                              fin);
+        k_residual64_to32<1><<<grid, dim3(kBX, kRY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials, fin);
     else
-        k_residual64_to32<0><<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials,
-                                                                              fin);
+        k_residual64_to32<0><<<grid, dim3(kBX, kRY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials, fin);
     return cudaGetLastError();
 }
 
