@@ -219,17 +219,23 @@ def job_rate(world: int, units_per_rank: float, max_ms: float) -> float:
     """Whole-job throughput: every rank processed units_per_rank in at most max_ms."""
     return world * units_per_rank / (max_ms * 1e-3)
 
-# Kernels lc_bench_kernel can time, and how many times each runs per step
-# (c = V-cycles in the step's five solves).
+# Kernels lc_bench_kernel can time (its kernel id), and how many launches of
+# each a step makes (c = V-cycles in the step's five solves, nu = nu1 + nu2).
 KERNELS = {
-    "fp64": [("k_smooth_colour<double,compact> (fine level, one colour phase)", lambda c, nu: 4 * nu * c),
-             ("k_rhs_stage (fused L(omega) + stage combination)", lambda c, nu: 5),
-             ("k_residual_restrict<double,compact> (fine level)", lambda c, nu: c)],
-    "mixed": [("k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)", lambda c, nu: c),
-              ("k_rhs_stage_mixed (FP32 L(omega) + FP64 stage combination)", lambda c, nu: 5),
-              ("k_residual64_to32<compact> (FP64 residual, rounded to FP32)", lambda c, nu: c + 5),
-              ("k_up<float,compact> (fine level: FP32 post-smoothing + FP64 psi += e)", lambda c, nu: c)],
+    "fp64": [(0, "k_smooth_colour<double,compact> (fine level, one colour phase)", lambda c, nu: 4 * nu * c),
+             (1, "k_rhs_stage (fused L(omega) + stage combination)", lambda c, nu: 5),
+             (2, "k_residual_restrict<double,compact> (fine level)", lambda c, nu: c)],
+    "mixed": [(0, "k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)", lambda c, nu: c),
+              (1, "k_rhs_stage_mixed (FP32 L(omega) + FP64 stage combination)", lambda c, nu: 5),
+              (2, "k_residual64_to32<compact> (FP64 residual, rounded to FP32)", lambda c, nu: c + 5),
+              (3, "k_up<float,compact> (fine level: FP32 post-smoothing + FP64 psi += e)", lambda c, nu: c)],
 }
+
+
+# DRAM bytes (read + write) of one launch of the roofline kernel, from one ncu
+# capture of the benchmark's own command (profiles/smoother_fp64_1024_traffic.md);
+# a kernel or grid size without an entry reports traffic null.
+MEASURED_TRAFFIC = {("k_smooth_colour<double,compact> (fine level, one colour phase)", 1024): 12728320 + 0}
 
 
 def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> dict:
@@ -241,9 +247,10 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
     p64 = fp64_peak_tflops(mhz)
     p32 = SMS * FP32_FMA_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12
     rows = []
-    for kid, (name, count) in enumerate(KERNELS[precision]):
+    nu = SCHEDULE["nu1"] + SCHEDULE["nu2"]
+    for kid, name, count in KERNELS[precision]:
         ms, nbytes, f64, f32 = lc.lc_bench_kernel(cav.handle, kid, 100)
-        share_ms = ms * count(cycles_per_step, SCHEDULE["nu1"] + SCHEDULE["nu2"])
+        share_ms = ms * count(cycles_per_step, nu)
         fr = {"hbm": nbytes / (ms * 1e-3) / 1e9 / hbm, "alu64": f64 / (ms * 1e-3) / 1e12 / p64,
               "alu32": f32 / (ms * 1e-3) / 1e12 / p32}
         rows.append((share_ms, kid, name, ms, nbytes, f64, f32, fr))
@@ -260,10 +267,10 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
                                 f"{'FP64' if bound == 'alu64' else 'FP32'} FMA/clk x 2 flop x {mhz:.0f} MHz "
                                 f"(median SM clock under load)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = MEASURED_TRAFFIC.get((name, cav.N))
     roof["kernel"] = name
     roof["kernel_ms"] = ms
-    roof["launches_per_step"] = KERNELS[precision][kid][1](cycles_per_step, SCHEDULE["nu1"] + SCHEDULE["nu2"])
+    roof["launches_per_step"] = {k: f for k, _, f in KERNELS[precision]}[kid](cycles_per_step, nu)
     roof["algorithmic_bytes"] = nbytes
     roof["fp64_flops"] = f64
     roof["fp32_flops"] = f32

@@ -62,7 +62,7 @@ extern "C" {
 #define LC_ERR_CUDA (-2)      /* a CUDA runtime call failed                          */
 #define LC_ERR_NOCONV (-3)    /* a Poisson solve hit max_cycles above its tolerance  */
 #define LC_ERR_NONFINITE (-4) /* NaN or Inf appeared in a residual or the state      */
-#define LC_ERR_TIMEOUT (-5)   /* reserved: a bounded device-side wait gave up        */
+#define LC_ERR_TIMEOUT (-5)   /* a bounded device-side wait (grid barrier) gave up   */
 #define LC_ERR_SIZE (-6)      /* buffer too small or size out of range               */
 #define LC_ERR_IO (-7)        /* checkpoint file could not be read or written        */
 
@@ -118,6 +118,16 @@ const char *lc_last_error(void);
  *                 n / n+1 superscripts fix (i outer, j inner), a "cycle" being
  *                 sor_sweeps sweeps followed by the stopping test.  FP64 only.
  *   "sor_sweeps"  sweeps per SOR cycle (16), 1..4096
+ *   "fused"       0 (default): one launch per fine-level FP64 colour phase;
+ *                 1: the colour phases of one smoothing pass run as one
+ *                 cooperative launch with a bounded grid barrier between
+ *                 phases (same values; LC_ERR_TIMEOUT if a barrier wait gave
+ *                 up).  On GB300 the barrier costs about what a launch does,
+ *                 so the default is 0.
+ *   "barrier_extra" test hook (0 default): 1 makes the fused smoother's grid
+ *                 barrier wait for one block more than the launch has, so
+ *                 every wait runs out (about 0.2 s each) and the next
+ *                 synchronising call reports LC_ERR_TIMEOUT
  *   "rhs64"       mixed precision only: 1 evaluates L(omega) (Eq. (8)) in FP64
  *                 from the FP64 psi and omega instead of their FP32 shadows
  *                 (default 0); the multigrid corrections stay FP32
@@ -209,8 +219,9 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * on the context stream.  FP64 precision: kernel 0 = fine-level smoother
  * colour phase (the colours taken in turn), 1 = fused L(omega) + stage
  * combination (stage 2), 2 = fine-level residual + full-weighting
- * restriction, 3 = one lexicographic SOR pass of sor_sweeps sweeps.  Mixed
- * precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
+ * restriction, 3 = one lexicographic SOR pass of sor_sweeps sweeps, 4 = the
+ * fine-level pre-smoothing pass (nu1 colour sweeps in one cooperative
+ * launch, LC_ERR_ARG where the device cannot launch it).  Mixed precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
  * residual, restriction), 1 = FP32 L(omega) + FP64 stage combination (stage
  * 2), 2 = FP64 residual rounded to FP32, 3 = fine-level FP32 tile kernel
  * (prolongation, post-smoothing, FP64 psi += e).  out[0] = mean ms per

@@ -153,6 +153,9 @@ struct lc_ctx {
     double beta = 1.0, U = 1.0;
     int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR
     int rhs64 = 0;                                      // mixed precision: L(omega) in FP64
+    int fused = 0;                 // 1: fine-level FP64 colour phases of a pass in one cooperative launch
+    int barrier_extra = 0;         // test hook: the fused kernel's barrier waits for this many more blocks
+    int fused_blocks[2] = {0, 0};  // its grid (beta == 1, beta != 1); 0: not available
     int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
     int tile_force = -1;                                // >= 0: one tile shape on every level
 
@@ -259,6 +262,28 @@ int enqueue_vcycle_phases(lc_ctx *c, cudaStream_t s) {
     return LC_OK;
 }
 
+// nsw smoothing sweeps of the fine FP64 level: one cooperative launch (the
+// colour phases separated by a grid barrier) when available, else one launch
+// per colour phase; the values are the same.  Returns the launch count, or a
+// negative error code.
+int enqueue_fine_sweeps(lc_ctx *c, cudaStream_t s, int nsw) {
+    const Layout &L = c->lay;
+    int nb = c->fused ? c->fused_blocks[c->beta != 1.0 ? 1 : 0] : 0;
+    if (nb > 0) {
+        cudaError_t e = launch_smooth_fused<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], nsw, c->beta,
+                                                    c->ds(), nb, c->barrier_extra);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_smooth_fused");
+        return 1;
+    }
+    int nc = c->op == LC_OP_COMPACT ? 4 : 2, k = 0;
+    for (int sw = 0; sw < nsw; ++sw)
+        for (int col = 0; col < nc; ++col, ++k) {
+            cudaError_t e = launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_smooth_colour");
+        }
+    return k;
+}
+
 FinishArgs finish_args(const lc_ctx *c, int nr, cudaGraphConditionalHandle h) {
     const Layout &L = c->lay;
     return FinishArgs{1, nr, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol, c->max_cycles};
@@ -273,16 +298,15 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
     *norm_done = false;
     if (!blocked_ok(c)) return enqueue_vcycle_phases(c, s);
     const Layout &L = c->lay;
-    int nc = c->op == LC_OP_COMPACT ? 4 : 2;
     int lc = coarse_level(c);
     bool phases0 = c->fine_phases && lc > 0;
     double *rpart = c->at<double>(L.rpart);
     int k = 0;
     for (int l = 0; l < lc; ++l) {
         if (l == 0 && phases0) {
-            for (int sw = 0; sw < c->nu1; ++sw)
-                for (int col = 0; col < nc; ++col, ++k)
-                    LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta));
+            int n = enqueue_fine_sweeps(c, s, c->nu1);
+            if (n < 0) return n;
+            k += n;
             LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], c->g(1),
                                                      c->psi(1), L.Pl[1]));
         } else {
@@ -299,9 +323,9 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
     for (int l = lc - 1; l >= 0; --l) {
         if (l == 0 && phases0) {
             LC_CUDA(launch_prolong_correct<double>(s, c->psi(0), L.Nl[0], L.Pl[0], c->psi(1), L.Pl[1]));
-            for (int sw = 0; sw < c->nu2; ++sw)
-                for (int col = 0; col < nc; ++col, ++k)
-                    LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], col, c->beta));
+            int n = enqueue_fine_sweeps(c, s, c->nu2);
+            if (n < 0) return n;
+            k += n;
         } else {
             LC_CUDA(launch_up<double>(s, tile_shape(c, l), c->op, c->psiB(l), c->g(l), c->psi(l + 1), L.Pl[l + 1],
                                       c->psi(l), L.Nl[l], L.Pl[l], c->nu2, c->beta, l == 0 ? rpart : nullptr, none,
@@ -492,7 +516,21 @@ int eager_step(lc_ctx *c) {
     return LC_OK;
 }
 
+int build_graph_once(lc_ctx *c);
+
+// Builds the step graph; if the fused cooperative smoother cannot be captured
+// or instantiated in it, falls back to one launch per colour phase.
 int build_graph(lc_ctx *c) {
+    int rc = build_graph_once(c);
+    if (rc != LC_OK && c->fused && (c->fused_blocks[0] || c->fused_blocks[1])) {
+        cudaGetLastError();  // clear a sticky launch error of the failed capture
+        c->fused_blocks[0] = c->fused_blocks[1] = 0;
+        rc = build_graph_once(c);
+    }
+    return rc;
+}
+
+int build_graph_once(lc_ctx *c) {
     release_graph(c);
     StagePlan st[5];
     stage_plan(c, st);
@@ -526,6 +564,8 @@ int ensure_init(lc_ctx *c) {
     LC_CUDA(cudaGetDevice(&c->device));
     LC_CUDA(init_mg_kernel_attributes());
     LC_CUDA(init_sor_kernel_attributes());
+    c->fused_blocks[0] = smooth_fused_blocks(c->op, false);
+    c->fused_blocks[1] = smooth_fused_blocks(c->op, true);
     if (!c->ws) {
         void *p = nullptr;
         LC_CUDA(cudaMalloc(&p, c->lay.total));
@@ -553,6 +593,12 @@ int sync_status(lc_ctx *c) {
         int zero = 0;
         LC_CUDA(cudaMemcpy(&c->ds()->status, &zero, sizeof(int), cudaMemcpyHostToDevice));
         if (status & kStatusNonFinite) return fail(LC_ERR_NONFINITE, "non-finite value in the Poisson residual or state");
+        if (status & kStatusTimeout) {
+            // a barrier that gave up left arrivals behind: start the next one from zero
+            unsigned zero2[2] = {0u, 0u};
+            LC_CUDA(cudaMemcpy(&c->ds()->bar_count, zero2, sizeof(unsigned), cudaMemcpyHostToDevice));
+            return fail(LC_ERR_TIMEOUT, "a device-side grid barrier wait gave up");
+        }
         if (status & kStatusNoConv) return fail(LC_ERR_NOCONV, "a Poisson solve reached max_cycles above tol");
     }
     return LC_OK;
@@ -681,6 +727,12 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "rhs64") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "rhs64 must be 0 or 1");
         c->rhs64 = iv;
+    } else if (k == "barrier_extra") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "barrier_extra must be 0 or 1");
+        c->barrier_extra = iv;
+    } else if (k == "fused") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "fused must be 0 or 1");
+        c->fused = iv;
     } else if (k == "sor_sweeps") {
         if (!integral || iv < 1 || iv > 4096) return fail(LC_ERR_ARG, "sor_sweeps must be 1..4096");
         c->sor_sweeps = iv;
@@ -866,7 +918,7 @@ int lc_launch_stats(lc_ctx *c, double out[2]) {
 
 int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
     LC_CHECK_CTX(c);
-    int nk = 4;
+    int nk = c->mixed() ? 4 : 5;
     if (!out || reps < 1 || kernel < 0 || kernel >= nk) return fail(LC_ERR_ARG, "bad kernel id, reps or output");
     int rc = ensure_init(c);
     if (rc) return rc;
@@ -889,8 +941,11 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 case 2:
                     return launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), N, P, c->g(1), c->psi(1),
                                                             L.Pl[1]);
-                default:
+                case 3:
                     return launch_sor_lex(s, c->op, c->psi(0), c->g(0), N, P, c->sor_sweeps, c->beta);
+                default:
+                    return launch_smooth_fused<double>(s, c->op, c->psi(0), c->g(0), N, P, c->nu1, c->beta, c->ds(),
+                                                       c->fused_blocks[c->beta != 1.0 ? 1 : 0], c->barrier_extra);
             }
         }
         switch (kernel) {
@@ -913,6 +968,8 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
     };
     if (c->mixed() && (kernel == 0 || kernel == 3) && coarse_level(c) == 0)
         return fail(LC_ERR_ARG, "grid too small for the tile kernels");
+    if (!c->mixed() && kernel == 4 && !c->fused_blocks[c->beta != 1.0 ? 1 : 0])
+        return fail(LC_ERR_ARG, "the fused smoother is not available on this device");
     cudaEvent_t e0, e1;
     LC_CUDA(cudaEventCreate(&e0));
     LC_CUDA(cudaEventCreate(&e1));
@@ -943,9 +1000,13 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 out[1] = 16.0 * n_int + 16.0 * n_c;
                 out[2] = res_flops * n_int + 8.0 * n_c;
                 break;
-            default:  // sor_sweeps sweeps; the grid is read and written once per launch
+            case 3:  // sor_sweeps sweeps; the grid is read and written once per launch
                 out[1] = 24.0 * n_int;
                 out[2] = c->sor_sweeps * (sw_flops + (c->beta != 1.0 ? 3.0 : 0.0)) * n_int;
+                break;
+            default:  // nu1 colour sweeps: psi and g read once, psi written once
+                out[1] = 24.0 * n_int;
+                out[2] = c->nu1 * (sw_flops + (c->beta != 1.0 ? 3.0 : 0.0)) * n_int;
         }
     } else {
         switch (kernel) {

@@ -33,6 +33,7 @@ constexpr int kMaxLevels = 16;
 
 constexpr int kStatusNoConv = 1;
 constexpr int kStatusNonFinite = 2;
+constexpr int kStatusTimeout = 4;  // a bounded device-side wait gave up
 
 // Device-resident solver state, one per context.
 struct DevState {
@@ -45,6 +46,7 @@ struct DevState {
     double mon[3];    // max|d omega|/dt, RES_psi, RES_omega
     unsigned int arrive;  // blocks that have written their residual partial (fused finisher)
     unsigned int pad1;
+    unsigned int bar_count, bar_gen;  // grid barrier of the fused smoother
     int log[kLogN];   // cycles per solve, ring buffer indexed by nsolves
 };
 
@@ -206,6 +208,17 @@ cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *
 constexpr int kRX = 30, kRY = 8;
 inline int residual_blocks_x(int N) { return (N - 1 + kRX - 1) / kRX; }
 int residual_norm_blocks(int N);
+// nsweeps colour sweeps of the fine-level smoother in one cooperative launch
+// of `blocks` co-resident blocks of 256 threads, a bounded grid barrier
+// between colour phases (same values as launch_smooth_colour, bit for bit).
+// extra: additional arrivals the barrier waits for (0; 1 only in the test
+// that makes the wait run out).
+template <typename T>
+cudaError_t launch_smooth_fused(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta,
+                                DevState *ds, int blocks, int extra);
+// Co-resident blocks of the fused smoother on the current device (0 if the
+// device cannot launch cooperative kernels).
+int smooth_fused_blocks(int op, bool relax);
 // nsw lexicographic SOR sweeps (Eq. (15) in its superscripts' order) in one
 // block, pipelined over wavefronts; psi in shared memory when
 // sor_smem_bytes(N, P) <= kMaxSmem.

@@ -75,11 +75,19 @@ __device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__rest
 // row, so the diagonal sum d4 = V(i+1) + V(i-1), with the column sums
 // V(k) = psi(k, j+1) + psi(k, j-1), takes V(i-1) from the lane to the left
 // (the same additions in the same order as gs_value, one fewer per node).
-template <typename T, int OP, bool RELAX>
-__global__ void __launch_bounds__(kBX *kBY)
-    k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
-    int a = blockIdx.x * blockDim.x + threadIdx.x;
-    int b = blockIdx.y * blockDim.y + threadIdx.y;
+//
+// colour_item does the work of thread (a, b) of a phase (a: the colour
+// node's column index, b: its row pair); the 32 lanes of a warp must hold 32
+// consecutive a of one b.  L2 = true reads psi through L2 (for the fused
+// kernel, whose blocks read values other blocks wrote in the same launch).
+template <bool L2, typename T>
+__device__ __forceinline__ T ldp(const T *p) {
+    return L2 ? __ldcg(p) : *p;
+}
+
+template <typename T, int OP, bool RELAX, bool L2>
+__device__ __forceinline__ void colour_item(T *psi, const T *__restrict__ g, int N, int P, int colour, T beta, int a,
+                                            int b) {
     int i, j;
     if (OP == 1) {
         i = ((colour & 1) ? 1 : 2) + 2 * a;
@@ -96,28 +104,28 @@ __global__ void __launch_bounds__(kBX *kBY)
         bool second = ok && j + 2 < N;
         size_t c = (size_t)j * P + i, c2 = c + 2 * (size_t)P;
         bool colr = rowok && i + 1 <= N;  // column i + 1 exists (it may be the wall)
-        T m_e = colr ? psi[c + P + 1] : T(0);
-        T m_c = ok ? psi[c + P] : T(0);
-        T Vr = colr ? m_e + psi[c - P + 1] : T(0);
-        T V2r = (colr && j + 2 < N) ? psi[c2 + P + 1] + m_e : T(0);
+        T m_e = colr ? ldp<L2>(psi + c + P + 1) : T(0);
+        T m_c = ok ? ldp<L2>(psi + c + P) : T(0);
+        T Vr = colr ? m_e + ldp<L2>(psi + c - P + 1) : T(0);
+        T V2r = (colr && j + 2 < N) ? ldp<L2>(psi + c2 + P + 1) + m_e : T(0);
         T Vl = __shfl_up_sync(0xffffffffu, Vr, 1), V2l = __shfl_up_sync(0xffffffffu, V2r, 1);
         if (!ok) return;
-        if (threadIdx.x == 0) {
-            T m_w = psi[c + P - 1];
-            Vl = m_w + psi[c - P - 1];
-            if (second) V2l = psi[c2 + P - 1] + m_w;
+        if ((threadIdx.x & 31) == 0) {
+            T m_w = ldp<L2>(psi + c + P - 1);
+            Vl = m_w + ldp<L2>(psi + c - P - 1);
+            if (second) V2l = ldp<L2>(psi + c2 + P - 1) + m_w;
         }
-        T n4 = (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]);
+        T n4 = (ldp<L2>(psi + c + 1) + ldp<L2>(psi + c - 1)) + (m_c + ldp<L2>(psi + c - P));
         T v1 = fma(T(0.2), n4, fma(T(0.05), Vr + Vl, g[c])), v2 = T(0);
         if (second) {
-            T n42 = (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c);
+            T n42 = (ldp<L2>(psi + c2 + 1) + ldp<L2>(psi + c2 - 1)) + (ldp<L2>(psi + c2 + P) + m_c);
             v2 = fma(T(0.2), n42, fma(T(0.05), V2r + V2l, g[c2]));
         }
         if (RELAX) {
-            T o1 = psi[c];
+            T o1 = ldp<L2>(psi + c);
             v1 = fma(beta, v1 - o1, o1);
             if (second) {
-                T o2 = psi[c2];
+                T o2 = ldp<L2>(psi + c2);
                 v2 = fma(beta, v2 - o2, o2);
             }
         }
@@ -129,19 +137,88 @@ __global__ void __launch_bounds__(kBX *kBY)
     size_t c = (size_t)j * P + i;
     bool second = j + 2 < N;
     size_t c2 = c + 2 * (size_t)P;
-    T m_c = psi[c + P];  // shared row j + 1
-    T v1 = fma(T(0.25), (psi[c + 1] + psi[c - 1]) + (m_c + psi[c - P]), g[c]), v2 = T(0);
-    if (second) v2 = fma(T(0.25), (psi[c2 + 1] + psi[c2 - 1]) + (psi[c2 + P] + m_c), g[c2]);
+    T m_c = ldp<L2>(psi + c + P);  // shared row j + 1
+    T v1 = fma(T(0.25), (ldp<L2>(psi + c + 1) + ldp<L2>(psi + c - 1)) + (m_c + ldp<L2>(psi + c - P)), g[c]),
+      v2 = T(0);
+    if (second)
+        v2 = fma(T(0.25), (ldp<L2>(psi + c2 + 1) + ldp<L2>(psi + c2 - 1)) + (ldp<L2>(psi + c2 + P) + m_c), g[c2]);
     if (RELAX) {
-        T o1 = psi[c];
+        T o1 = ldp<L2>(psi + c);
         v1 = fma(beta, v1 - o1, o1);
         if (second) {
-            T o2 = psi[c2];
+            T o2 = ldp<L2>(psi + c2);
             v2 = fma(beta, v2 - o2, o2);
         }
     }
     psi[c] = v1;
     if (second) psi[c2] = v2;
+}
+
+template <typename T, int OP, bool RELAX>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
+    colour_item<T, OP, RELAX, false>(psi, g, N, P, colour, beta, blockIdx.x * blockDim.x + threadIdx.x,
+                                     blockIdx.y * blockDim.y + threadIdx.y);
+}
+
+// Grid-wide barrier between the colour phases of a cooperative launch (all
+// blocks co-resident).  Every wait is bounded: after kBarCycles SM clock
+// cycles (about 0.2 s) a block gives up, sets kStatusTimeout (reported as
+// LC_ERR_TIMEOUT; the host then resets the count) and goes on, so the kernel
+// always ends.  The last block to arrive resets the count before it releases
+// the others, so the next barrier starts from zero.  `expected` is the number
+// of arrivals that releases the barrier (gridDim.x; one more only in the
+// test that makes the wait run out).
+constexpr long long kBarCycles = 400000000LL;
+__device__ __forceinline__ void grid_barrier(DevState *ds, unsigned expected) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &ds->bar_gen;
+        unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(&ds->bar_count, 1u) == expected - 1) {
+            ds->bar_count = 0;
+            __threadfence();
+            atomicAdd(&ds->bar_gen, 1u);
+        } else {
+            long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > kBarCycles) {
+                    atomicOr(&ds->status, kStatusTimeout);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// nsweeps colour sweeps of the smoother in one cooperative launch: the
+// threads of phase (a, b) of k_smooth_colour become warp-sized items (a warp:
+// 32 consecutive a of one b); each block takes an equal contiguous share of
+// the items, so the SMs get equal FP64 work, and a grid barrier separates the
+// phases.  Same per-node expression and colour order as the one-launch-per-
+// phase form, so the same bits, without a launch per phase.
+template <typename T, int OP, bool RELAX>
+__global__ void __launch_bounds__(256)
+    k_smooth_fused(T *psi, const T *__restrict__ g, int N, int P, int nsweeps, T beta, DevState *ds, int extra) {
+    const int na = N / 2;                              // colour nodes per row: at most N / 2
+    const int nb = OP == 1 ? (N / 2 + 1) / 2 : N / 2;  // row pairs
+    const int nchunk = (na + 31) / 32, items = nchunk * nb;
+    const int lo = (int)((long long)items * blockIdx.x / gridDim.x);
+    const int hi = (int)((long long)items * (blockIdx.x + 1) / gridDim.x);
+    const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int ncol = OP == 1 ? 4 : 2;
+    for (int s = 0; s < nsweeps; ++s)
+        for (int col = 0; col < ncol; ++col) {
+            if (s > 0 || col > 0) grid_barrier(ds, gridDim.x + extra);
+            for (int w = lo + wib; w < hi; w += nwb) {
+                int b = w / nchunk, a = (w - b * nchunk) * 32 + lane;
+                colour_item<T, OP, RELAX, true>(psi, g, N, P, col, beta, a, b);
+            }
+        }
 }
 
 // Residual of the fine level, full-weighted onto the coarse level; also zeroes
@@ -662,6 +739,47 @@ cudaError_t init_sor_kernel_attributes() {
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_sor_lex_cluster<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSorClusterSmem);
     return e;
+}
+
+template <typename T, int OP, bool RELAX>
+static cudaError_t fused_t(cudaStream_t s, T *psi, const T *g, int N, int P, int nsweeps, T beta, DevState *ds,
+                           int blocks, int extra) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_smooth_fused<T, OP, RELAX>, psi, g, N, P, nsweeps, beta, ds, extra);
+}
+
+template <typename T>
+cudaError_t launch_smooth_fused(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta,
+                                DevState *ds, int blocks, int extra) {
+    bool relax = beta != T(1);
+    if (op == 1)
+        return relax ? fused_t<T, 1, true>(s, psi, g, N, P, nsweeps, beta, ds, blocks, extra)
+                     : fused_t<T, 1, false>(s, psi, g, N, P, nsweeps, beta, ds, blocks, extra);
+    return relax ? fused_t<T, 0, true>(s, psi, g, N, P, nsweeps, beta, ds, blocks, extra)
+                 : fused_t<T, 0, false>(s, psi, g, N, P, nsweeps, beta, ds, blocks, extra);
+}
+template cudaError_t launch_smooth_fused<double>(cudaStream_t, int, double *, const double *, int, int, int, double,
+                                                 DevState *, int, int);
+
+int smooth_fused_blocks(int op, bool relax) {
+    int dev = 0, coop = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    const void *k = op == 1 ? (relax ? (const void *)k_smooth_fused<double, 1, true> : (const void *)k_smooth_fused<double, 1, false>)
+                            : (relax ? (const void *)k_smooth_fused<double, 0, true> : (const void *)k_smooth_fused<double, 0, false>);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 256, 0) != cudaSuccess) return 0;
+    // two blocks per SM: enough warps to keep the FP64 pipe busy, few barrier arrivals
+    return (per < 2 ? per : 2) * sms;
 }
 
 #define LCX_INSTANTIATE(T)                                                                                           \

@@ -117,3 +117,15 @@ def test_batch_errors():
     with pytest.raises(lc.LCError) as e:
         b.synchronize()
     assert e.value.code == lc.LC_ERR_NOCONV
+
+
+def test_batch_of_256_cavities_the_maximum():
+    """The largest batch (256 cavities): the first and the last give the bits
+    of single contexts."""
+    Ns = [128] * 255 + [256]
+    Res = [1000.0 + 100.0 * k for k in range(256)]
+    b = lc.Batch(Ns, Res)
+    b.step(1)
+    for c in (0, 255):
+        ref = singles([Ns[c]], [Res[c]], 1)[0]
+        assert np.array_equal(b.psi(c), ref[0]) and np.array_equal(b.omega(c), ref[1])

@@ -213,6 +213,7 @@ MODES = {
     "phases": dict(blocked=0),
     "tiles": dict(blocked=1, fine_phases=0, coarse_max=2),
     "tiles+fine-phases": dict(blocked=1, fine_phases=1, coarse_max=4),
+    "tiles+fine-phases-fused": dict(blocked=1, fine_phases=1, coarse_max=4, fused=1),
     "coarse-block": dict(blocked=1, fine_phases=0, coarse_max=64),
     "tiles110x54": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0),
     "tiles110x22": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1),
@@ -260,3 +261,62 @@ def test_1024_big_tiles_one_step_matches_oracle(fine_phases):
     # oracle's unfused arithmetic and the GPU's FMAs differ at ~1e-12 of it
     assert rel(g.psi(), r.psi()) < 1e-10 and rel(g.omega(), r.omega()) < 1e-10
     assert np.array_equal(g.cycle_log(), r.cycle_log())
+
+
+def test_fused_smoother_equals_phase_launches_at_1024():
+    """The cooperative fine-level smoother (colour phases separated by a grid
+    barrier) gives the bits of one launch per colour phase."""
+    a = lc.Cavity(1024, 10000.0, fused=1)
+    b = lc.Cavity(1024, 10000.0, fused=0)
+    a.step(2)
+    b.step(2)
+    assert np.array_equal(a.cycle_log(), b.cycle_log())
+    assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
+
+
+def test_fused_barrier_timeout_is_reported_and_context_recovers():
+    """A barrier that waits for a block that never arrives gives up after its
+    bound (about 0.2 s), the host reads LC_ERR_TIMEOUT, and the context steps
+    on correctly afterwards."""
+    N = 256
+    g = lc.Cavity(N, 1000.0, nu1=1, fused=1)
+    g.step(1)
+    g.synchronize()
+    g.set_option("barrier_extra", 1)  # only for the two stand-alone passes below, never inside a step
+    lc.lc_bench_kernel(g.handle, 4, 1)  # one warm-up and one timed fused pass, each with 3 barriers
+    with pytest.raises(lc.LCError) as e:
+        g.synchronize()
+    assert e.value.code == lc.LC_ERR_TIMEOUT
+    g.set_option("barrier_extra", 0)
+    ref = lc.Cavity(N, 1000.0, nu1=1, fused=1)
+    psi, om = smooth_random_state(N, seed=9)
+    g.set_state(psi, om)
+    ref.set_state(psi, om)
+    g.step(2)
+    ref.step(2)
+    assert np.array_equal(g.psi(), ref.psi()) and np.array_equal(g.omega(), ref.omega())
+
+
+def test_maximum_grid_8192_mirror_equivariance():
+    """The largest accepted grid, N = 8192 (8193^2 nodes, 537 MB per FP64
+    field): one step with the lid moving each way gives mirror-image bits,
+    which checks every index of every level at that size."""
+    N = 8192
+    a = lc.Cavity(N, 10000.0)
+    a.step(1)
+    pa, wa = a.psi(), a.omega()
+    a.close()
+    b = lc.Cavity(N, 10000.0, U=-1.0)
+    b.step(1)
+    assert np.array_equal(b.psi(), -pa[:, ::-1]) and np.array_equal(b.omega(), -wa[:, ::-1])
+    assert np.abs(pa).max() > 0.0
+
+
+@pytest.mark.parametrize("precision", [lc.LC_PREC_FP64, lc.LC_PREC_MIXED])
+def test_lid_at_rest_keeps_the_fluid_at_rest(precision):
+    """U = 0: the degenerate cavity has zero right-hand sides everywhere; every
+    solve stops after its first cycle and the state stays exactly zero."""
+    g = lc.Cavity(128, 1000.0, precision=precision, U=0.0)
+    g.step(3)
+    assert not g.psi().any() and not g.omega().any()
+    assert (g.cycle_log() == 1).all()
