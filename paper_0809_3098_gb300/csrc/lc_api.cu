@@ -495,13 +495,16 @@ int capture_stage(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
 // from the host (one stream sync per cycle).  Used for per-kernel profiling:
 // kernels inside a graph with conditional nodes cannot be profiled.
 int eager_step(lc_ctx *c) {
+    static const char *kStageName[5] = {"stage 1", "stage 2", "stage 3", "stage 4", "stage 5"};
     cudaStream_t s = c->stream();
     StagePlan st[5];
     stage_plan(c, st);
     for (int k = 0; k < 5; ++k) {
+        NvtxRange stage_range(kStageName[k]);
         int rc = enqueue_stage_head(c, s, st[k]);
         if (rc) return rc;
         for (;;) {
+            NvtxRange cycle_range("poisson cycle");
             rc = enqueue_cycle_body(c, s, 0);
             if (rc) return rc;
             int more = 0;
@@ -781,6 +784,7 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
 int lc_step(lc_ctx *c, int nsteps) {
     LC_CHECK_CTX(c);
     if (nsteps < 0) return fail(LC_ERR_ARG, "nsteps must be >= 0");
+    NvtxRange range("lc_step");
     int rc = ensure_init(c);
     if (rc) return rc;
     if (c->use_graph && c->graph_dirty) {

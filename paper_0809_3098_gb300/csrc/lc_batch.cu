@@ -409,11 +409,14 @@ int build_graph(lc_batch *b) {
 }
 
 int eager_step(lc_batch *b) {
+    static const char *kStageName[5] = {"stage 1", "stage 2", "stage 3", "stage 4", "stage 5"};
     cudaStream_t s = b->stream();
     for (int k = 0; k < 5; ++k) {
+        NvtxRange stage_range(kStageName[k]);
         int rc = enqueue_head(b, s, k);
         if (rc) return rc;
         for (;;) {
+            NvtxRange cycle_range("poisson cycle");
             rc = enqueue_cycle(b, s, 0);
             if (rc) return rc;
             int more = 0;
@@ -626,6 +629,7 @@ int lc_batch_bind_workspace(lc_batch *b, void *dev_ptr, size_t bytes) {
 int lc_batch_step(lc_batch *b, int nsteps) {
     LB_CHECK(b);
     if (nsteps < 0) return bfail(LC_ERR_ARG, "nsteps must be >= 0");
+    NvtxRange range("lc_batch_step");
     int rc = binit(b);
     if (rc) return rc;
     if (b->use_graph && b->dirty) {

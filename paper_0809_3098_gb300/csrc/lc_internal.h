@@ -26,7 +26,17 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX: ranges for profilers, no-ops without one
+
 namespace lcx {
+
+// Profiler range for the enclosing scope (NVTX push / pop).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kLogN = 65536;
 constexpr int kMaxLevels = 16;
@@ -384,7 +394,6 @@ cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const B
                                   int nblocks, double *rpart, const double *gpart, BatchFinish fin);
 cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U);
 cudaError_t launch_psi32_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks);
-cudaError_t launch_to32_batch(cudaStream_t s, BatchCav *cav, int c);
 
 // Sets the calling thread's lc_last_error() message.
 void set_last_error(const char *msg);

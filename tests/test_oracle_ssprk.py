@@ -100,6 +100,14 @@ def test_stability_polynomial_is_taylor_to_fourth_order():
     ratios = np.array(ratios)
     assert np.ptp(ratios) < 1e-10 * max(1.0, abs(ratios).max())
     assert 0 < ratios[0] < 1 / 120  # an SSP(5,4) method damps the z^5 term below exp's
+    # and that constant is b^T A^4 e of the Butcher tableau of the paper's
+    # printed table (with the reading of alpha[2][1]): R(z) = 1 + z b^T (I - zA)^-1 e
+    pa, pb = _paper_table()
+    pa[2, 1] = 1.0 - pa[2, 0]
+    pb[1, 0] = 0.391752226571890
+    A, b, _ = _butcher(pa, pb)
+    c5 = b @ np.linalg.matrix_power(A, 4) @ np.ones(5)
+    assert abs(ratios[0] - c5) < 1e-9 * c5
 
 
 def test_global_order_four_on_nonlinear_ode():
