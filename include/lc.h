@@ -144,7 +144,20 @@ const char *lc_last_error(void);
  *                 uses one launch per colour phase (no recomputed halo).
  *   "coarse_max"  levels with at most this many intervals run as one V-cycle
  *                 in a single thread block (default -1: 32 for FP64, 64 for
- *                 mixed precision), 2..256.
+ *                 mixed precision), 2..256; used where the cluster form below
+ *                 is off or does not apply.
+ *   "coarse_cluster" the coarse V-cycle on a thread-block cluster of this
+ *                 many blocks, one per SM (-1 default: in FP64 16, else 8,
+ *                 whichever the device schedules, in mixed precision off;
+ *                 0 off; 2..16): its levels of more than
+ *                 cluster_split intervals are split by rows over the blocks
+ *                 (barrier between colour phases), the rest run in the first
+ *                 block.  Same values as the one-block form.
+ *   "cluster_max" the cluster form takes over from the first level below the
+ *                 fine one with at most this many intervals (default -1: 128),
+ *                 8..512, if its arrays fit shared memory
+ *   "cluster_split" levels of at most this many intervals run in the
+ *                 cluster's first block alone (16), 4..256
  *   "tile_shape"  -1 (default) picks each level's tile shape; 0..3 forces
  *                 the shared-memory tiles of 110x54, 110x22, 46x22 or 16x16
  *                 owned nodes, 4 the 44x20 register tiles held by one warp

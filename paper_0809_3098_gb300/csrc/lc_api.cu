@@ -158,6 +158,9 @@ struct lc_ctx {
     int fused_blocks[2] = {0, 0};  // its grid (beta == 1, beta != 1); 0: not available
     int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
     int tile_force = -1;                                // >= 0: one tile shape on every level
+    int coarse_cluster = -1;  // coarse V-cycle on a cluster of this many blocks; -1: auto (FP64), 0: off
+    int cluster_max = -1;     // first level run by the cluster kernel: N_l <= cluster_max (-1: 128)
+    int cluster_split = 16;   // levels of <= cluster_split intervals run in the cluster's first block alone
 
     Layout lay;
     char *ws = nullptr;
@@ -211,11 +214,32 @@ void release_graph(lc_ctx *c) {
     c->graph_dirty = true;
 }
 
-// First level handled by the one-block coarse V-cycle (N_l <= coarse_max and
-// small enough for shared memory).
+// Blocks of the coarse cluster kernel; by default it runs in FP64 only (the
+// FP32 one-block V-cycle is faster than the cluster's barriers).
+int cluster_size(const lc_ctx *c) {
+    if (c->coarse_cluster >= 0) return c->coarse_cluster;
+    return c->mixed() ? 0 : coarse_cluster_size();
+}
+
+// Whether coarse level lc runs on the cluster kernel: it is not the fine level
+// (whose last kernel takes the residual norm) and it has levels to split.
+bool cluster_coarse(const lc_ctx *c, int lc) {
+    int C = cluster_size(c), elem = c->mixed() ? 4 : 8;
+    int cmax = c->cluster_max > 0 ? c->cluster_max : 128;
+    const Layout &L = c->lay;
+    return C > 0 && lc >= 1 && L.Nl[lc] <= cmax && L.Nl[lc] > c->cluster_split &&
+           cluster_smem_bytes(L.Nl[lc], L.nlev - lc, C, c->cluster_split, elem) <= kMaxSmem - 1024;
+}
+
+// First level handled by the coarse V-cycle kernel: the first level below the
+// fine one that the cluster kernel takes (N_l <= cluster_max) when it is on,
+// else the first with N_l <= coarse_max small enough for one block's shared
+// memory.
 int coarse_level(const lc_ctx *c) {
     const Layout &L = c->lay;
     int elem = c->mixed() ? 4 : 8;
+    for (int l = 1; l < L.nlev; ++l)
+        if (cluster_coarse(c, l)) return l;
     int cmax = c->coarse_max > 0 ? c->coarse_max : (c->mixed() ? 64 : 32);
     for (int l = 0; l < L.nlev; ++l)
         if (L.Nl[l] <= cmax && coarse_smem_bytes(L.Nl[l], L.nlev - l, elem) <= kMaxSmem - 1024) return l;
@@ -315,9 +339,14 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
         }
         ++k;
     }
-    LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], lc == 0 ? c->psi(0) : nullptr, c->psi(lc), L.Pl[lc],
-                                  L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, lc == 0 ? rpart : nullptr,
-                                  lc == 0 ? finish_args(c, 1, h) : kNoFinish));
+    if (cluster_coarse(c, lc))
+        LC_CUDA(launch_coarse_cluster<double>(s, c->op, c->g(lc), L.Pl[lc], c->psi(lc), L.Pl[lc], L.Nl[lc],
+                                              L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, cluster_size(c),
+                                              c->cluster_split));
+    else
+        LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], lc == 0 ? c->psi(0) : nullptr, c->psi(lc),
+                                      L.Pl[lc], L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta,
+                                      lc == 0 ? rpart : nullptr, lc == 0 ? finish_args(c, 1, h) : kNoFinish));
     ++k;
     Correct64 none{nullptr, 0, nullptr, 0};
     for (int l = lc - 1; l >= 0; --l) {
@@ -350,8 +379,13 @@ int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h
     for (int l = 0; l < lc; ++l, ++k)
         LC_CUDA(launch_down<float>(s, tile_shape(c, l), c->op, nullptr, 1, c->g32(l), c->eB(l), L.Nl[l], L.Pl[l],
                                    c->g32(l + 1), L.Pl[l + 1], c->nu1, beta));
-    LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc], L.nlev - lc,
-                                 c->nu1, c->nu2, c->nuc, beta, nullptr, kNoFinish));
+    if (cluster_coarse(c, lc))
+        LC_CUDA(launch_coarse_cluster<float>(s, c->op, c->g32(lc), L.Pl[lc], c->eA(lc), L.Pl[lc], L.Nl[lc],
+                                             L.nlev - lc, c->nu1, c->nu2, c->nuc, beta, cluster_size(c),
+                                             c->cluster_split));
+    else
+        LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc],
+                                     L.nlev - lc, c->nu1, c->nu2, c->nuc, beta, nullptr, kNoFinish));
     ++k;
     if (lc == 0) {
         LC_CUDA(launch_correct64(s, c->eA(0), L.Pl[0], c->psi(0), L.Pl[0], nullptr, L.Pl[0], c->N));
@@ -766,6 +800,16 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "coarse_max") {
         if (!integral || iv < 2 || iv > 256) return fail(LC_ERR_ARG, "coarse_max must be 2..256");
         c->coarse_max = iv;
+    } else if (k == "coarse_cluster") {
+        if (!integral || iv < -1 || iv == 1 || iv > 16)
+            return fail(LC_ERR_ARG, "coarse_cluster must be -1 (auto), 0 (off) or 2..16");
+        c->coarse_cluster = iv;
+    } else if (k == "cluster_max") {
+        if (!integral || iv < 8 || iv > 512) return fail(LC_ERR_ARG, "cluster_max must be 8..512");
+        c->cluster_max = iv;
+    } else if (k == "cluster_split") {
+        if (!integral || iv < 4 || iv > 256) return fail(LC_ERR_ARG, "cluster_split must be 4..256");
+        c->cluster_split = iv;
     } else if (k == "graph") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "graph must be 0 or 1");
         c->use_graph = iv;

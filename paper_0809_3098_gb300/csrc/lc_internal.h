@@ -278,6 +278,15 @@ template <typename T>
 cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T *psi_warm, T *psi_out, int Po, int N0,
                           int nl, int nu1, int nu2, int nuc, T beta, double *partial, FinishArgs fin);
 
+// The coarse V-cycle on a cluster of C blocks (lc_mg.cu): levels of more
+// than `split` intervals split by rows over the blocks, the rest in block 0;
+// the same values as launch_coarse with psi_warm = nullptr and no norm.
+size_t cluster_smem_bytes(int N0, int nl, int C, int split, int elem);
+template <typename T>
+cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg, T *psi_out, int Po, int N0, int nl,
+                                  int nu1, int nu2, int nuc, T beta, int C, int split);
+int coarse_cluster_size();  // 16, 8, or 0 when the device cannot run the cluster kernel
+
 constexpr size_t kMaxSmem = 227 * 1024;
 cudaError_t init_mg_kernel_attributes();
 

@@ -22,6 +22,8 @@
 // tile ever sees a neighbour's half-updated values.
 #include "lc_internal.h"
 
+#include <cooperative_groups.h>
+
 namespace lcx {
 
 namespace {
@@ -398,25 +400,157 @@ __device__ __forceinline__ void cs_update(T *sp, const T *sg, int c, int LP, T b
     sp[c] = v;
 }
 
+// FP64 loops of the one-block levels take their nodes packed into whole
+// warps: on GB300 an FP64 warp instruction occupies its SM sub-partition's
+// FP64 unit for about 64 clocks however few lanes are active, so a phase of a
+// few dozen nodes costs (FP64 instructions per warp) x 64 clocks on the
+// busiest sub-partition, and half-empty warps double it.  The nodes of a
+// phase are independent, so the order of the work does not change a value.
+template <typename T>
+constexpr bool kPacked = sizeof(T) == 8;
+
 template <typename T, int OP>
 __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
     int LP = n + 1, m = n - 1;
-    for (int s = 0; s < nu; ++s)
-        for (int col = 0; col < (OP == 1 ? 4 : 2); ++col) {
-            if (OP == 1) {
-                int x0 = (col & 1) ? 1 : 2, y0 = (col >> 1) ? 1 : 2;
-                for (int y = y0 + 2 * (int)threadIdx.y; y <= m; y += 2 * blockDim.y)
-                    for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
-                        cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
-            } else {
-                for (int y = 1 + threadIdx.y; y <= m; y += blockDim.y) {
-                    int x0 = ((1 + y) & 1) == col ? 1 : 2;
-                    for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
-                        cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+    if constexpr (kPacked<T>) {
+        const unsigned tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+        for (int s = 0; s < nu; ++s)
+            for (int col = 0; col < (OP == 1 ? 4 : 2); ++col) {
+                if (OP == 1) {
+                    const int x0 = (col & 1) ? 1 : 2, y0 = (col >> 1) ? 1 : 2;
+                    const unsigned nx = m >= x0 ? (m - x0) / 2 + 1 : 0, ny = m >= y0 ? (m - y0) / 2 + 1 : 0;
+                    for (unsigned q = tid; q < nx * ny; q += nt) {
+                        const unsigned yy = q / nx, xx = q - yy * nx;
+                        cs_update<T, OP>(sp, sg, (y0 + 2 * (int)yy) * LP + x0 + 2 * (int)xx, LP, beta);
+                    }
+                } else {
+                    const unsigned hx = (m + 1) / 2;  // most nodes of one colour in a row
+                    for (unsigned q = tid; q < (unsigned)m * hx; q += nt) {
+                        const unsigned yy = q / hx, k = q - yy * hx;
+                        const int y = 1 + (int)yy, x = (((1 + y) & 1) == col ? 1 : 2) + 2 * (int)k;
+                        if (x <= m) cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+                    }
                 }
+                __syncthreads();
+            }
+    } else {
+        for (int s = 0; s < nu; ++s)
+            for (int col = 0; col < (OP == 1 ? 4 : 2); ++col) {
+                if (OP == 1) {
+                    int x0 = (col & 1) ? 1 : 2, y0 = (col >> 1) ? 1 : 2;
+                    for (int y = y0 + 2 * (int)threadIdx.y; y <= m; y += 2 * blockDim.y)
+                        for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
+                            cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+                } else {
+                    for (int y = 1 + threadIdx.y; y <= m; y += blockDim.y) {
+                        int x0 = ((1 + y) & 1) == col ? 1 : 2;
+                        for (int x = x0 + 2 * (int)threadIdx.x; x <= m; x += 2 * blockDim.x)
+                            cs_update<T, OP>(sp, sg, y * LP + x, LP, beta);
+                    }
+                }
+                __syncthreads();
+            }
+    }
+}
+
+// Full weighting of the residual sr around fine node (2X, 2Y) onto coarse
+// node (X, Y); the coarse correction starts from zero.
+template <typename T>
+__device__ __forceinline__ void restrict_node(const T *sr, int LP, T *sgc, T *spc, int LPc, int X, int Y) {
+    const T *r = sr + (2 * Y) * LP + 2 * X;
+    T e4 = (r[1] + r[-1]) + (r[LP] + r[-LP]);
+    T d4 = (r[LP + 1] + r[LP - 1]) + (r[-LP + 1] + r[-LP - 1]);
+    sgc[Y * LPc + X] = fma(T(0.5), e4, fma(T(0.25), d4, r[0]));
+    spc[Y * LPc + X] = T(0);
+}
+
+// Bilinear prolongation of the coarse correction ec onto fine node (i, j),
+// added to psi.
+template <typename T>
+__device__ __forceinline__ void prolong_add(T *sp, const T *ec, int LP, int LPc, int i, int j) {
+    int I = i >> 1, J = j >> 1, cc = J * LPc + I;
+    T e;
+    if (!(i & 1) && !(j & 1))
+        e = ec[cc];
+    else if ((i & 1) && !(j & 1))
+        e = mul_rn(T(0.5), ec[cc] + ec[cc + 1]);
+    else if (!(i & 1) && (j & 1))
+        e = mul_rn(T(0.5), ec[cc] + ec[cc + LPc]);
+    else
+        e = mul_rn(T(0.25), (ec[cc] + ec[cc + 1]) + (ec[cc + LPc] + ec[cc + LPc + 1]));
+    sp[j * LP + i] = add_rn(sp[j * LP + i], e);
+}
+
+// A V-cycle over nl levels held in shared memory from base: psi and g of each
+// level ((n + 1)^2 each, n = N0 >> k), level after level, boundaries zero;
+// sr is residual scratch of (N0 + 1)^2.  psi and g of the top level are set
+// on entry; the coarser levels' psi is reset here.  The whole block runs it.
+template <typename T, int OP>
+__device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int nu1, int nu2, int nuc, T beta) {
+    int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
+    const int tid = ty * bx + tx, nt = bx * by;
+    // down
+    int off = 0;
+    for (int k = 0; k + 1 < nl; ++k) {
+        int n = N0 >> k, LP = n + 1, nc = n / 2, LPc = nc + 1;
+        T *sp = base + off, *sg = sp + LP * LP;
+        T *spc = sg + LP * LP, *sgc = spc + LPc * LPc;
+        cs_sweeps<T, OP>(sp, sg, n, nu1, beta);
+        if constexpr (kPacked<T>) {
+            const unsigned m = n - 1, mc = nc - 1;
+            for (unsigned q = tid; q < m * m; q += nt) {
+                const unsigned yy = q / m;
+                const int c = (1 + (int)yy) * LP + 1 + (int)(q - yy * m);
+                sr[c] = gs_local<T, OP>(sp, sg, c, LP) - sp[c];
+            }
+            for (int q = tid; q < 4 * n; q += nt) {  // the boundary ring
+                const int side = q / n, k = q - side * n;
+                sr[side == 0 ? k : side == 1 ? n * LP + k + 1 : side == 2 ? (k + 1) * LP : k * LP + n] = T(0);
             }
             __syncthreads();
+            for (unsigned q = tid; q < mc * mc; q += nt) {
+                const unsigned yy = q / mc;
+                restrict_node<T>(sr, LP, sgc, spc, LPc, 1 + (int)(q - yy * mc), 1 + (int)yy);
+            }
+            __syncthreads();
+        } else {
+            for (int y = ty; y <= n; y += by)
+                for (int x = tx; x <= n; x += bx) {
+                    int q = y * LP + x;
+                    sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? gs_local<T, OP>(sp, sg, q, LP) - sp[q] : T(0);
+                }
+            __syncthreads();
+            for (int Y = 1 + ty; Y < nc; Y += by)
+                for (int X = 1 + tx; X < nc; X += bx) restrict_node<T>(sr, LP, sgc, spc, LPc, X, Y);
+            __syncthreads();
         }
+        off += 2 * LP * LP;
+    }
+    {
+        int n = N0 >> (nl - 1), LP = n + 1;
+        T *sp = base + off, *sg = sp + LP * LP;
+        // with one unknown and beta = 1 a single sweep is already exact
+        cs_sweeps<T, OP>(sp, sg, n, (n == 2 && beta == T(1)) ? 1 : nuc, beta);
+    }
+    // up
+    for (int k = nl - 2; k >= 0; --k) {
+        int n = N0 >> k, LP = n + 1, LPc = n / 2 + 1;
+        off -= 2 * LP * LP;
+        T *sp = base + off, *sg = sp + LP * LP;
+        const T *ec = sg + LP * LP;
+        const unsigned m = n - 1;
+        if constexpr (kPacked<T>) {
+            for (unsigned q = tid; q < m * m; q += nt) {
+                const unsigned jj = q / m;
+                prolong_add<T>(sp, ec, LP, LPc, 1 + (int)(q - jj * m), 1 + (int)jj);
+            }
+        } else {
+            for (int j = 1 + ty; j < n; j += by)
+                for (int i = 1 + tx; i < n; i += bx) prolong_add<T>(sp, ec, LP, LPc, i, j);
+        }
+        __syncthreads();
+        cs_sweeps<T, OP>(sp, sg, n, nu2, beta);
+    }
 }
 
 template <typename T, int OP>
@@ -438,59 +572,7 @@ __device__ __forceinline__ double coarse_body(const T *__restrict__ g_in, int Pg
             if (psi_warm) base[y * L0 + x] = psi_warm[(size_t)y * Po + x];
         }
     __syncthreads();
-    // down
-    int off = 0;
-    for (int k = 0; k + 1 < nl; ++k) {
-        int n = N0 >> k, LP = n + 1, nc = n / 2, LPc = nc + 1;
-        T *sp = base + off, *sg = sp + LP * LP;
-        T *spc = sg + LP * LP, *sgc = spc + LPc * LPc;
-        cs_sweeps<T, OP>(sp, sg, n, nu1, beta);
-        for (int y = ty; y <= n; y += by)
-            for (int x = tx; x <= n; x += bx) {
-                int q = y * LP + x;
-                sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? gs_local<T, OP>(sp, sg, q, LP) - sp[q] : T(0);
-            }
-        __syncthreads();
-        for (int Y = 1 + ty; Y < nc; Y += by)
-            for (int X = 1 + tx; X < nc; X += bx) {
-                const T *r = sr + (2 * Y) * LP + 2 * X;
-                T e4 = (r[1] + r[-1]) + (r[LP] + r[-LP]);
-                T d4 = (r[LP + 1] + r[LP - 1]) + (r[-LP + 1] + r[-LP - 1]);
-                sgc[Y * LPc + X] = fma(T(0.5), e4, fma(T(0.25), d4, r[0]));
-                spc[Y * LPc + X] = T(0);
-            }
-        __syncthreads();
-        off += 2 * LP * LP;
-    }
-    {
-        int n = N0 >> (nl - 1), LP = n + 1;
-        T *sp = base + off, *sg = sp + LP * LP;
-        // with one unknown and beta = 1 a single sweep is already exact
-        cs_sweeps<T, OP>(sp, sg, n, (n == 2 && beta == T(1)) ? 1 : nuc, beta);
-    }
-    // up
-    for (int k = nl - 2; k >= 0; --k) {
-        int n = N0 >> k, LP = n + 1, LPc = n / 2 + 1;
-        off -= 2 * LP * LP;
-        T *sp = base + off, *sg = sp + LP * LP;
-        const T *ec = sg + LP * LP;
-        for (int j = 1 + ty; j < n; j += by)
-            for (int i = 1 + tx; i < n; i += bx) {
-                int I = i >> 1, J = j >> 1, cc = J * LPc + I;
-                T e;
-                if (!(i & 1) && !(j & 1))
-                    e = ec[cc];
-                else if ((i & 1) && !(j & 1))
-                    e = mul_rn(T(0.5), ec[cc] + ec[cc + 1]);
-                else if (!(i & 1) && (j & 1))
-                    e = mul_rn(T(0.5), ec[cc] + ec[cc + LPc]);
-                else
-                    e = mul_rn(T(0.25), (ec[cc] + ec[cc + 1]) + (ec[cc + LPc] + ec[cc + LPc + 1]));
-                sp[j * LP + i] = add_rn(sp[j * LP + i], e);
-            }
-        __syncthreads();
-        cs_sweeps<T, OP>(sp, sg, n, nu2, beta);
-    }
+    smem_vcycle<T, OP>(base, sr, N0, nl, nu1, nu2, nuc, beta);
     double acc = 0.0;
     for (int y = 1 + ty; y < N0; y += by)
         for (int x = 1 + tx; x < N0; x += bx) {
@@ -589,6 +671,228 @@ __global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, i
     int lc = cv.lc;
     coarse_body<float, OP>(cv.g32[lc], cv.P[lc], nullptr, cv.eA[lc], cv.P[lc], cv.N >> lc, cv.nlev - lc, nu1, nu2, nuc,
                            beta, false, smem_raw);
+}
+
+// ---------------------------------------------------------------------------
+// The coarse V-cycle on a thread-block cluster.  On GB300 one SM retires about
+// two FP64 operations per clock, so a one-block V-cycle over levels of 32^2
+// nodes and more is bound by a single SM's FP64 (or, in FP32, issue) rate.
+// Here the levels above a threshold are split by rows over the C blocks of
+// one cluster (one block per SM), with a cluster barrier between phases; the
+// levels at or below the threshold run in block 0 alone (smem_vcycle).
+//
+// Block r's strip of a level is rows [lo, hi) of psi, g and the residual; psi
+// has one halo row on each side.  A block that updates a node of its first or
+// last row also writes the new value into the neighbour block's halo copy
+// (distributed shared memory); same-colour nodes are never neighbours, so no
+// block reads a value that is being written in the same phase, and the
+// barrier's release / acquire makes the copies visible before the next one.
+// Restriction and prolongation read the rows they need from whichever block
+// owns them.  Every value is computed by the expression the one-block kernel
+// uses for it, so both kernels give the same bits.
+// Shared-memory layout of k_coarse_cluster (element offsets, the same in
+// every block): the strips of the nd distributed levels (psi with its two
+// halo rows, g, residual), then the one-block levels in smem_vcycle's layout
+// (used by block 0), its residual scratch, and one row of zeros.
+struct ClusterPlan {
+    int N0, nl, nd, C;
+    int psi[kMaxLevels], g[kMaxLevels], r[kMaxLevels];
+    int single, sr, zero, total;
+};
+
+struct Strip {
+    int lo, hi;
+    bool on;
+};
+
+// Rows [lo, hi) of the interior rows [1, m] owned by block r of C: the first
+// A = min(C, m) blocks take floor or ceil(m / A) rows each, the rest none.
+__device__ __forceinline__ Strip strip_of(int m, int C, int r) {
+    int A = min(C, m);
+    if (r >= A) return Strip{0, 0, false};
+    return Strip{1 + (r * m) / A, 1 + ((r + 1) * m) / A, true};
+}
+
+// The block whose strip holds interior row y (1 <= y <= m).
+__device__ __forceinline__ int row_owner(int y, int m, int C) {
+    int A = min(C, m);
+    return (y * A + m - 1) / m - 1;
+}
+
+// One colour phase over a strip: the nodes and the order of cs_sweeps.
+template <typename T, int OP>
+__device__ __forceinline__ void strip_phase(T *ps, const T *gs, int n, Strip st, int col, T beta, T *up, T *dn) {
+    const int LP = n + 1, m = n - 1;
+    const int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
+    if (OP == 1) {
+        const int py = col >> 1, x0 = (col & 1) ? 1 : 2;
+        const int y0 = st.lo + ((st.lo & 1) != py);
+        for (int y = y0 + 2 * ty; y < st.hi; y += 2 * by) {
+            T *row = ps + (y - st.lo + 1) * LP;
+            const T *grow = gs + (y - st.lo) * LP;
+            T *cu = y == st.lo ? up : nullptr, *cd = y == st.hi - 1 ? dn : nullptr;
+            for (int x = x0 + 2 * tx; x <= m; x += 2 * bx) {
+                T v = gs_local<T, OP>(row, grow, x, LP);
+                if (beta != T(1)) v = fma(beta, v - row[x], row[x]);
+                row[x] = v;
+                if (cu) cu[x] = v;
+                if (cd) cd[x] = v;
+            }
+        }
+    } else {
+        for (int y = st.lo + ty; y < st.hi; y += by) {
+            T *row = ps + (y - st.lo + 1) * LP;
+            const T *grow = gs + (y - st.lo) * LP;
+            T *cu = y == st.lo ? up : nullptr, *cd = y == st.hi - 1 ? dn : nullptr;
+            const int x0 = ((1 + y) & 1) == col ? 1 : 2;
+            for (int x = x0 + 2 * tx; x <= m; x += 2 * bx) {
+                T v = gs_local<T, OP>(row, grow, x, LP);
+                if (beta != T(1)) v = fma(beta, v - row[x], row[x]);
+                row[x] = v;
+                if (cu) cu[x] = v;
+                if (cd) cd[x] = v;
+            }
+        }
+    }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(512)
+    k_coarse_cluster(const T *__restrict__ g_in, int Pg, T *__restrict__ psi_out, int Po, int nu1, int nu2, int nuc,
+                     T beta, ClusterPlan pl) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sm = reinterpret_cast<T *>(smem_raw);
+    const int C = pl.C, rank = (int)cl.block_rank();
+    const int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
+    const int tid = ty * bx + tx, nt = bx * by;
+    const int ncol = OP == 1 ? 4 : 2;
+
+    for (int q = tid; q < pl.total; q += nt) sm[q] = T(0);
+    __syncthreads();
+    {
+        const int n = pl.N0, LP = n + 1;
+        const Strip st = strip_of(n - 1, C, rank);
+        T *gs = sm + pl.g[0];
+        if (st.on)
+            for (int y = st.lo + ty; y < st.hi; y += by)
+                for (int x = 1 + tx; x < n; x += bx) gs[(y - st.lo) * LP + x] = g_in[(size_t)y * Pg + x];
+    }
+    cl.sync();  // every block's arrays are set before any block writes a halo row
+
+    // down: smoothing, residual and restriction on the distributed levels
+    for (int k = 0; k < pl.nd; ++k) {
+        const int n = pl.N0 >> k, m = n - 1, LP = n + 1;
+        const int nc = n / 2, mc = nc - 1, LPc = nc + 1;
+        const Strip st = strip_of(m, C, rank);
+        T *ps = sm + pl.psi[k], *gs = sm + pl.g[k], *rs = sm + pl.r[k];
+        T *up = nullptr, *dn = nullptr;
+        if (st.on && rank > 0) {
+            const Strip sa = strip_of(m, C, rank - 1);
+            up = cl.map_shared_rank(ps + (sa.hi - sa.lo + 1) * LP, rank - 1);
+        }
+        if (st.on && strip_of(m, C, rank + 1).on) dn = cl.map_shared_rank(ps, rank + 1);
+        for (int s = 0; s < nu1; ++s)
+            for (int col = 0; col < ncol; ++col) {
+                strip_phase<T, OP>(ps, gs, n, st, col, beta, up, dn);
+                cl.sync();
+            }
+        if (st.on)
+            for (int y = st.lo + ty; y < st.hi; y += by) {
+                const T *row = ps + (y - st.lo + 1) * LP, *grow = gs + (y - st.lo) * LP;
+                T *rrow = rs + (y - st.lo) * LP;
+                for (int x = 1 + tx; x <= m; x += bx) rrow[x] = gs_local<T, OP>(row, grow, x, LP) - row[x];
+            }
+        cl.sync();
+        // full weighting of the residual rows 2Y - 1, 2Y, 2Y + 1 (owned by any block)
+        const bool single = k + 1 == pl.nd;
+        const Strip sc = single ? Strip{rank == 0 ? 1 : 0, rank == 0 ? nc : 0, rank == 0} : strip_of(mc, C, rank);
+        if (sc.on) {
+            T *pc = single ? sm + pl.single : sm + pl.psi[k + 1];
+            T *gc = single ? pc + LPc * LPc : sm + pl.g[k + 1];
+            const int yoff = single ? 0 : sc.lo;  // local row of coarse row Y in gc: Y - yoff
+            if (!single)
+                for (int q = tid; q < (sc.hi - sc.lo + 2) * LPc; q += nt) pc[q] = T(0);
+            auto rrow = [&](int y) -> const T * {
+                const int o = row_owner(y, m, C);
+                return cl.map_shared_rank(rs + (y - strip_of(m, C, o).lo) * LP, o);
+            };
+            for (int Y = sc.lo + ty; Y < sc.hi; Y += by) {
+                const T *rS = rrow(2 * Y - 1), *r0 = rrow(2 * Y), *rN = rrow(2 * Y + 1);
+                for (int X = 1 + tx; X <= mc; X += bx) {
+                    const int x = 2 * X;
+                    T e4 = (r0[x + 1] + r0[x - 1]) + (rN[x] + rS[x]);
+                    T d4 = (rN[x + 1] + rN[x - 1]) + (rS[x + 1] + rS[x - 1]);
+                    gc[(Y - yoff) * LPc + X] = fma(T(0.5), e4, fma(T(0.25), d4, r0[x]));
+                    if (single) pc[Y * LPc + X] = T(0);
+                }
+            }
+        }
+        cl.sync();
+    }
+
+    // the levels at or below the threshold, in block 0
+    if (rank == 0)
+        smem_vcycle<T, OP>(sm + pl.single, sm + pl.sr, pl.N0 >> pl.nd, pl.nl - pl.nd, nu1, nu2, nuc, beta);
+    cl.sync();
+
+    // up: prolongation of the coarser level's correction, then smoothing
+    for (int k = pl.nd - 1; k >= 0; --k) {
+        const int n = pl.N0 >> k, m = n - 1, LP = n + 1;
+        const int nc = n / 2, mc = nc - 1, LPc = nc + 1;
+        const Strip st = strip_of(m, C, rank);
+        const bool single = k + 1 == pl.nd;
+        T *ps = sm + pl.psi[k], *gs = sm + pl.g[k];
+        if (st.on) {
+            // own rows and both halo rows (the owners add the same correction
+            // to the same value, so the copies stay equal)
+            const int ylo = max(1, st.lo - 1), yhi = min(m, st.hi);
+            auto crow = [&](int J) -> const T * {
+                if (single) return cl.map_shared_rank(sm + pl.single + J * LPc, 0);
+                if (J == 0 || J == nc) return sm + pl.zero;
+                const int o = row_owner(J, mc, C);
+                return cl.map_shared_rank(sm + pl.psi[k + 1] + (J - strip_of(mc, C, o).lo + 1) * LPc, o);
+            };
+            for (int j = ylo + ty; j <= yhi; j += by) {
+                const T *c0 = crow(j >> 1), *c1 = crow((j >> 1) + 1);
+                T *row = ps + (j - st.lo + 1) * LP;
+                for (int i = 1 + tx; i <= m; i += bx) {
+                    const int I = i >> 1;
+                    T e;
+                    if (!(i & 1) && !(j & 1))
+                        e = c0[I];
+                    else if ((i & 1) && !(j & 1))
+                        e = mul_rn(T(0.5), c0[I] + c0[I + 1]);
+                    else if (!(i & 1) && (j & 1))
+                        e = mul_rn(T(0.5), c0[I] + c1[I]);
+                    else
+                        e = mul_rn(T(0.25), (c0[I] + c0[I + 1]) + (c1[I] + c1[I + 1]));
+                    row[i] = add_rn(row[i], e);
+                }
+            }
+        }
+        cl.sync();
+        T *up = nullptr, *dn = nullptr;
+        if (st.on && rank > 0) {
+            const Strip sa = strip_of(m, C, rank - 1);
+            up = cl.map_shared_rank(ps + (sa.hi - sa.lo + 1) * LP, rank - 1);
+        }
+        if (st.on && strip_of(m, C, rank + 1).on) dn = cl.map_shared_rank(ps, rank + 1);
+        for (int s = 0; s < nu2; ++s)
+            for (int col = 0; col < ncol; ++col) {
+                strip_phase<T, OP>(ps, gs, n, st, col, beta, up, dn);
+                cl.sync();
+            }
+    }
+    {
+        const int n = pl.N0, LP = n + 1;
+        const Strip st = strip_of(n - 1, C, rank);
+        const T *ps = sm + pl.psi[0];
+        if (st.on)
+            for (int y = st.lo + ty; y < st.hi; y += by)
+                for (int x = 1 + tx; x < n; x += bx) psi_out[(size_t)y * Po + x] = ps[(y - st.lo + 1) * LP + x];
+    }
 }
 
 constexpr int kShapeTX[5] = {110, 110, 46, 16, 44};
@@ -711,6 +1015,95 @@ cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T
     return cudaGetLastError();
 }
 
+// Blocks of a cluster share one SM only if their shared memory fits it
+// twice; every launch requests at least this much, so each block gets an SM
+// (and its FP64 pipe) of its own.
+constexpr size_t kClusterMinSmem = 120 * 1024;
+
+static ClusterPlan cluster_plan(int N0, int nl, int C, int split) {
+    ClusterPlan pl{};
+    pl.N0 = N0;
+    pl.nl = nl;
+    pl.C = C;
+    pl.nd = 0;
+    while (pl.nd < nl - 1 && (N0 >> pl.nd) > split) ++pl.nd;
+    int off = 0;
+    auto take = [&off](int n) {
+        int o = off;
+        off += (n + 3) & ~3;
+        return o;
+    };
+    for (int k = 0; k < pl.nd; ++k) {
+        int n = N0 >> k, m = n - 1, A = m < C ? m : C, H = (m + A - 1) / A, LP = n + 1;
+        pl.psi[k] = take((H + 2) * LP);
+        pl.g[k] = take(H * LP);
+        pl.r[k] = take(H * LP);
+    }
+    int single = 0;
+    for (int k = pl.nd; k < nl; ++k) single += 2 * ((N0 >> k) + 1) * ((N0 >> k) + 1);
+    pl.single = take(single);
+    pl.sr = take(((N0 >> pl.nd) + 1) * ((N0 >> pl.nd) + 1));
+    pl.zero = take(N0 + 2);
+    pl.total = off;
+    return pl;
+}
+
+size_t cluster_smem_bytes(int N0, int nl, int C, int split, int elem) {
+    size_t b = (size_t)cluster_plan(N0, nl, C, split).total * elem;
+    return b < kClusterMinSmem ? kClusterMinSmem : b;
+}
+
+template <typename T>
+cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg, T *psi_out, int Po, int N0, int nl,
+                                  int nu1, int nu2, int nuc, T beta, int C, int split) {
+    ClusterPlan pl = cluster_plan(N0, nl, C, split);
+    size_t sm = cluster_smem_bytes(N0, nl, C, split, sizeof(T));
+    if (pl.nd < 1 || C < 1 || C > 16 || sm > kMaxSmem - 1024) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(32, 16);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (op == 1) return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 1>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
+    return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 0>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
+}
+
+// Largest cluster (16, else 8, else 0) that the device can schedule for the
+// coarse cluster kernel with its minimum shared memory.
+int coarse_cluster_size() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    int best = 0;
+    for (int C : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(32, 16);
+        cfg.dynamicSmemBytes = kMaxSmem - 1024;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_coarse_cluster<double, 1>, &cfg) == cudaSuccess && n > 0) {
+            best = C;
+            break;
+        }
+        cudaGetLastError();  // a size the device cannot schedule is not an error here
+    }
+    cached = best;
+    return best;
+}
+
 namespace {
 
 template <int OP, int TX, int TY>
@@ -810,8 +1203,21 @@ static cudaError_t set_batch_attrs_t() {
     return cudaSuccess;
 }
 
+template <typename T>
+static cudaError_t set_cluster_attrs_t() {
+    const void *k[] = {(const void *)k_coarse_cluster<T, 0>, (const void *)k_coarse_cluster<T, 1>};
+    for (const void *f : k) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kMaxSmem - 1024));
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t init_mg_kernel_attributes() {
     cudaError_t e = set_attrs_t<double>();
+    if (e == cudaSuccess) e = set_cluster_attrs_t<double>();
+    if (e == cudaSuccess) e = set_cluster_attrs_t<float>();
     if (e == cudaSuccess) e = set_attrs_t<float>();
     if (e == cudaSuccess) e = set_batch_attrs_t<0>();
     if (e == cudaSuccess) e = set_batch_attrs_t<1>();
@@ -824,7 +1230,9 @@ cudaError_t init_mg_kernel_attributes() {
     template cudaError_t launch_up<T>(cudaStream_t, int, int, const T *, const T *, const T *, int, T *, int, int,     \
                                       int, T, double *, Correct64, FinishArgs);                                       \
     template cudaError_t launch_coarse<T>(cudaStream_t, int, const T *, int, const T *, T *, int, int, int, int, int,  \
-                                          int, T, double *, FinishArgs);
+                                          int, T, double *, FinishArgs);                                              \
+    template cudaError_t launch_coarse_cluster<T>(cudaStream_t, int, const T *, int, T *, int, int, int, int, int,    \
+                                                  int, T, int, int);
 LCX_MG_INSTANTIATE(double)
 LCX_MG_INSTANTIATE(float)
 

@@ -128,3 +128,19 @@ def test_mixed_tile_shapes_bitwise_identical(shape, N, op, nu):
     b.step(2)
     assert np.array_equal(a.cycle_log(), b.cycle_log())
     assert np.array_equal(a.psi(), b.psi()) and np.array_equal(a.omega(), b.omega())
+
+
+@pytest.mark.parametrize("N,op", [(384, lc.LC_OP_COMPACT), (256, lc.LC_OP_COMPACT), (320, lc.LC_OP_5PT),
+                                  (1024, lc.LC_OP_COMPACT)])
+def test_mixed_cluster_coarse_bitwise_identical(N, op):
+    """FP32 coarse V-cycle on a cluster of 16, 8 or 3 blocks against the
+    one-block form: the same bits."""
+    runs = []
+    for opts in (dict(coarse_cluster=0), dict(coarse_cluster=16, cluster_max=256), dict(coarse_cluster=8),
+                 dict(coarse_cluster=3, cluster_split=8)):
+        g = lc.Cavity(N, 5000.0, precision=MIXED, op=op, **opts)
+        g.step(2)
+        runs.append((g.psi(), g.omega(), g.cycle_log()))
+    for p, w, cyc in runs[1:]:
+        assert np.array_equal(cyc, runs[0][2])
+        assert np.array_equal(p, runs[0][0]) and np.array_equal(w, runs[0][1])

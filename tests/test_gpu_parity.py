@@ -209,15 +209,22 @@ def test_runs_on_torch_stream_in_order():
     assert g.params["steps"] == 4
 
 
+NOCL = dict(coarse_cluster=0)  # the one-block coarse V-cycle
 MODES = {
     "phases": dict(blocked=0),
-    "tiles": dict(blocked=1, fine_phases=0, coarse_max=2),
-    "tiles+fine-phases": dict(blocked=1, fine_phases=1, coarse_max=4),
-    "tiles+fine-phases-fused": dict(blocked=1, fine_phases=1, coarse_max=4, fused=1),
-    "coarse-block": dict(blocked=1, fine_phases=0, coarse_max=64),
-    "tiles110x54": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0),
-    "tiles110x22": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1),
-    "tiles16x16": dict(blocked=1, fine_phases=0, coarse_max=2, tile_shape=3),
+    "tiles": dict(blocked=1, fine_phases=0, coarse_max=2, **NOCL),
+    "tiles+fine-phases": dict(blocked=1, fine_phases=1, coarse_max=4, **NOCL),
+    "tiles+fine-phases-fused": dict(blocked=1, fine_phases=1, coarse_max=4, fused=1, **NOCL),
+    "coarse-block": dict(blocked=1, fine_phases=0, coarse_max=64, **NOCL),
+    "tiles110x54": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=0, **NOCL),
+    "tiles110x22": dict(blocked=1, fine_phases=0, coarse_max=4, tile_shape=1, **NOCL),
+    "tiles16x16": dict(blocked=1, fine_phases=0, coarse_max=2, tile_shape=3, **NOCL),
+    # coarse levels on a thread-block cluster: strips of 1..16 rows, uneven
+    # splits (3 and 5 blocks), and the largest level the shared memory takes
+    "cluster16": dict(blocked=1, fine_phases=1, coarse_cluster=16, cluster_max=256),
+    "cluster3-split8": dict(blocked=1, fine_phases=0, coarse_cluster=3, cluster_max=64, cluster_split=8),
+    "cluster5-split4": dict(blocked=1, fine_phases=1, coarse_cluster=5, cluster_max=512, cluster_split=4),
+    "cluster8-split32": dict(blocked=1, fine_phases=1, coarse_cluster=8, cluster_split=32),
 }
 
 
