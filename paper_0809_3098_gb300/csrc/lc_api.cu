@@ -412,7 +412,7 @@ int enqueue_cycle_body(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) 
     if (c->solver == 1) {  // one pass of sor_sweeps lexicographic sweeps, then the stopping test
         LC_CUDA(launch_sor_lex(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->sor_sweeps, c->beta));
         LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<double>(L.rpart),
-                                             finish_args(c, L.nrpart_grid, h)));
+                                             finish_args(c, residual_norm64_blocks(c->N), h)));
         c->kernels_per_cycle = 2;
         return LC_OK;
     }
@@ -421,7 +421,7 @@ int enqueue_cycle_body(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h) 
     if (rc) return rc;
     if (!norm_done) {
         LC_CUDA(launch_residual_norm<double>(s, c->op, c->psi(0), c->g(0), c->N, L.Pl[0], c->at<double>(L.rpart),
-                                             finish_args(c, L.nrpart_grid, h)));
+                                             finish_args(c, residual_norm64_blocks(c->N), h)));
         c->kernels_per_cycle += 1;
     }
     return LC_OK;

@@ -218,6 +218,10 @@ cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *
 constexpr int kRX = 30, kRY = 8;
 inline int residual_blocks_x(int N) { return (N - 1 + kRX - 1) / kRX; }
 int residual_norm_blocks(int N);
+// k_residual_norm (the FP64 stopping test) sums kNormRows rows per thread;
+// its launch has residual_norm64_blocks(N) <= residual_norm_blocks(N) blocks.
+constexpr int kNormRows = 4;
+int residual_norm64_blocks(int N);
 // nsweeps colour sweeps of the fine-level smoother in one cooperative launch
 // of `blocks` co-resident blocks of 256 threads, a bounded grid barrier
 // between colour phases (same values as launch_smooth_colour, bit for bit).

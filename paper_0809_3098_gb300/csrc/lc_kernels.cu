@@ -300,20 +300,26 @@ __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, 
 }
 
 // Per-block partial sums of rho^2 over interior nodes (FP64 accumulation); a
-// block of 32 x 8 threads covers 30 x 8 interior nodes (rho_halo: the outer
-// lanes of each warp are halo).
+// block of 32 x 8 threads covers 30 x (8 kNormRows) interior nodes (rho_halo:
+// the outer lanes of each warp are halo).  Each thread accumulates kNormRows
+// rows, kRY apart, before the block sum: the sum's FP64 additions are warp
+// instructions of ~64 clocks each on GB300 however few lanes they serve, so
+// one reduction per kNormRows rows instead of one per row.
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials,
                     FinishArgs fin) {
     __shared__ double sh[32];
     int i0 = 1 + blockIdx.x * kRX;
-    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    int j0 = 1 + blockIdx.y * (kRY * kNormRows) + threadIdx.y;
     double v = 0.0;
-    T rho;
-    if (rho_halo<T, OP>(psi, g, N, P, i0, j, rho)) {
-        double r = (double)rho;
-        v = r * r;
+#pragma unroll
+    for (int k = 0; k < kNormRows; ++k) {  // warp-uniform: rho_halo's shuffles see every lane
+        T rho;
+        if (rho_halo<T, OP>(psi, g, N, P, i0, j0 + k * kRY, rho)) {
+            double r = (double)rho;
+            v = fma(r, r, v);
+        }
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) partials[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -532,13 +538,16 @@ cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, i
 }
 
 int residual_norm_blocks(int N) { return residual_blocks_x(N) * ((N - 1 + kRY - 1) / kRY); }
+int residual_norm64_blocks(int N) {
+    return residual_blocks_x(N) * ((N - 1 + kRY * kNormRows - 1) / (kRY * kNormRows));
+}
 int assemble_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY - 1) / kBY); }
 int monitor_blocks(int N) { return ((N + 1 + kBX - 1) / kBX) * ((N + 1 + kBY - 1) / kBY); }
 
 template <typename T>
 cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *g, int N, int P, double *partials,
                                  FinishArgs fin) {
-    dim3 grid(residual_blocks_x(N), (N - 1 + kRY - 1) / kRY), blk(kBX, kRY);
+    dim3 grid(residual_blocks_x(N), (N - 1 + kRY * kNormRows - 1) / (kRY * kNormRows)), blk(kBX, kRY);
     if (op == 1)
         k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
     else
