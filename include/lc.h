@@ -163,6 +163,10 @@ const char *lc_last_error(void);
  *                 owned nodes, 4 the 44x20 register tiles held by one warp
  *                 each (mixed precision, nu1, nu2 <= 2 with the compact
  *                 operator; elsewhere a forced 4 falls back to the default).
+ *   "pdl"         1 (default): the step's kernels are launched with
+ *                 programmatic dependent launch (each waits for its
+ *                 predecessor on entry; the launch overlaps the predecessor's
+ *                 drain; 1-2% per step); 0: plain stream order.  Same values.
  *   "graph"       1 (default) replays each step as one CUDA graph whose
  *                 V-cycle loops are device-side while-nodes; 0 launches the
  *                 same kernels one by one and drives the V-cycle loop from the
@@ -265,7 +269,7 @@ void lc_batch_destroy(lc_batch *b);
 
 /* Options as lc_set_option: "op", "coarse_max" (8..64) [before first use],
  * "nu1", "nu2" (1..4), "nuc", "beta", "max_cycles", "U", "advect", "rhs64",
- * "graph". */
+ * "pdl", "graph". */
 int lc_batch_set_option(lc_batch *b, const char *key, double value);
 int lc_batch_set_stream(lc_batch *b, void *cuda_stream);
 size_t lc_batch_workspace_bytes(int count, const int *N, int precision);

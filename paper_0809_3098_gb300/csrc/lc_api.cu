@@ -161,6 +161,8 @@ struct lc_ctx {
     int coarse_cluster = -1;  // coarse V-cycle on a cluster of this many blocks; -1: auto (FP64), 0: off
     int cluster_max = -1;     // first level run by the cluster kernel: N_l <= cluster_max (-1: 128)
     int cluster_split = 16;   // levels of <= cluster_split intervals run in the cluster's first block alone
+    int pdl = 1;                   // launch the step's kernels with programmatic dependent launch
+    bool pdl_unsupported = false;  // a graph with PDL edges failed to build: kernels launch one after another
 
     Layout lay;
     char *ws = nullptr;
@@ -530,6 +532,7 @@ int capture_stage(lc_ctx *c, cudaStream_t s, const StagePlan &st) {
 // kernels inside a graph with conditional nodes cannot be profiled.
 int eager_step(lc_ctx *c) {
     static const char *kStageName[5] = {"stage 1", "stage 2", "stage 3", "stage 4", "stage 5"};
+    PdlScope pdl(c->pdl);
     cudaStream_t s = c->stream();
     StagePlan st[5];
     stage_plan(c, st);
@@ -555,14 +558,26 @@ int eager_step(lc_ctx *c) {
 
 int build_graph_once(lc_ctx *c);
 
-// Builds the step graph; if the fused cooperative smoother cannot be captured
-// or instantiated in it, falls back to one launch per colour phase.
+// Builds the step graph.  If it cannot be captured or instantiated with
+// programmatic-dependent-launch edges, it is built again without them; if the
+// fused cooperative smoother is the obstacle, with one launch per colour
+// phase.
 int build_graph(lc_ctx *c) {
-    int rc = build_graph_once(c);
-    if (rc != LC_OK && c->fused && (c->fused_blocks[0] || c->fused_blocks[1])) {
-        cudaGetLastError();  // clear a sticky launch error of the failed capture
-        c->fused_blocks[0] = c->fused_blocks[1] = 0;
-        rc = build_graph_once(c);
+    int rc = LC_OK;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+        {
+            PdlScope pdl(c->pdl && !c->pdl_unsupported);
+            rc = build_graph_once(c);
+        }
+        if (rc == LC_OK) break;
+        cudaGetLastError();  // clear a launch error of the failed capture
+        if (c->pdl && !c->pdl_unsupported) {
+            c->pdl_unsupported = true;
+        } else if (c->fused && (c->fused_blocks[0] || c->fused_blocks[1])) {
+            c->fused_blocks[0] = c->fused_blocks[1] = 0;
+        } else {
+            break;
+        }
     }
     return rc;
 }
@@ -800,6 +815,10 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "coarse_max") {
         if (!integral || iv < 2 || iv > 256) return fail(LC_ERR_ARG, "coarse_max must be 2..256");
         c->coarse_max = iv;
+    } else if (k == "pdl") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "pdl must be 0 or 1");
+        c->pdl = iv;
+        c->pdl_unsupported = false;
     } else if (k == "coarse_cluster") {
         if (!integral || iv < -1 || iv == 1 || iv > 16)
             return fail(LC_ERR_ARG, "coarse_cluster must be -1 (auto), 0 (off) or 2..16");

@@ -75,6 +75,8 @@ struct lc_batch {
     double tol = 1e-10, beta = 1.0, U = 1.0;
     int op = LC_OP_COMPACT, nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
     int use_graph = 1, rhs64 = 0;
+    int pdl = 1;                   // programmatic dependent launch of the step's kernels
+    bool pdl_unsupported = false;  // a graph with PDL edges failed to build
     int Lmax = 0;
     std::vector<int> shape;  // tile shape per level (< Lmax)
 
@@ -347,7 +349,25 @@ int enqueue_head(lc_batch *b, cudaStream_t s, int stage) {
     return LC_OK;
 }
 
+int build_graph_once(lc_batch *b);
+
+// Builds the step graph, without programmatic-dependent-launch edges if it
+// cannot be built with them.
 int build_graph(lc_batch *b) {
+    int rc;
+    {
+        PdlScope pdl(b->pdl && !b->pdl_unsupported);
+        rc = build_graph_once(b);
+    }
+    if (rc != LC_OK && b->pdl && !b->pdl_unsupported) {
+        cudaGetLastError();  // clear a launch error of the failed capture
+        b->pdl_unsupported = true;
+        rc = build_graph_once(b);
+    }
+    return rc;
+}
+
+int build_graph_once(lc_batch *b) {
     release_graph(b);
     cudaStream_t s;
     LB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -410,6 +430,7 @@ int build_graph(lc_batch *b) {
 
 int eager_step(lc_batch *b) {
     static const char *kStageName[5] = {"stage 1", "stage 2", "stage 3", "stage 4", "stage 5"};
+    PdlScope pdl(b->pdl);
     cudaStream_t s = b->stream();
     for (int k = 0; k < 5; ++k) {
         NvtxRange stage_range(kStageName[k]);
@@ -581,6 +602,10 @@ int lc_batch_set_option(lc_batch *b, const char *key, double v) {
     } else if (k == "rhs64") {
         if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "rhs64 must be 0 or 1");
         b->rhs64 = iv;
+    } else if (k == "pdl") {
+        if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "pdl must be 0 or 1");
+        b->pdl = iv;
+        b->pdl_unsupported = false;
     } else if (k == "graph") {
         if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "graph must be 0 or 1");
         b->use_graph = iv;

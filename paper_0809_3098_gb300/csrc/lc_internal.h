@@ -70,6 +70,44 @@ struct StageCoef {
     int mode;
 };
 
+// ---- programmatic dependent launch (PDL)
+// Every kernel of the step starts with pdl_enter(): it waits until the
+// previous kernel in the stream has finished and its writes are visible.
+// Launched with the programmatic-stream-serialization attribute (launch_pdl
+// under a PdlScope), a kernel is launched once its predecessor's blocks have
+// all exited, without waiting for the predecessor's completion to be
+// processed, and nothing touches global memory before the wait; for a kernel
+// launched without the attribute the wait does nothing.  No kernel triggers
+// its dependents early: an explicit trigger at kernel entry, which lets the
+// next grid's blocks occupy the SMs while the current one runs, made the
+// FP64 step 25% slower on GB300, where this form saves 1-2%.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+extern thread_local int tl_pdl;
+struct PdlScope {
+    int prev;
+    explicit PdlScope(int on) : prev(tl_pdl) { tl_pdl = on; }
+    ~PdlScope() { tl_pdl = prev; }
+    PdlScope(const PdlScope &) = delete;
+    PdlScope &operator=(const PdlScope &) = delete;
+};
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = tl_pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Arguments of the end-of-cycle decision that the last block of a kernel
 // producing residual partials takes (enabled = 0: partials only).  The last
 // block sums the nr residual partials and the ng right-hand-side partials in

@@ -18,6 +18,8 @@
 
 namespace lcx {
 
+thread_local int tl_pdl = 0;
+
 namespace {
 
 constexpr int kBX = 32, kBY = 8;
@@ -157,6 +159,7 @@ __device__ __forceinline__ void colour_item(T *psi, const T *__restrict__ g, int
 template <typename T, int OP, bool RELAX>
 __global__ void __launch_bounds__(kBX *kBY)
     k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
+    pdl_enter();
     colour_item<T, OP, RELAX, false>(psi, g, N, P, colour, beta, blockIdx.x * blockDim.x + threadIdx.x,
                                      blockIdx.y * blockDim.y + threadIdx.y);
 }
@@ -229,6 +232,7 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(kRT *kRT)
     k_residual_restrict(const T *__restrict__ psi, const T *__restrict__ g, int Nf, int Pf, T *__restrict__ gc,
                         T *__restrict__ psic, int Pc) {
+    pdl_enter();
     __shared__ T rho[2 * kRT + 1][2 * kRT + 2];
     int Nc = Nf / 2;
     int I0 = 1 + blockIdx.x * kRT, J0 = 1 + blockIdx.y * kRT;
@@ -259,6 +263,7 @@ __global__ void __launch_bounds__(kRT *kRT)
 template <typename T>
 __global__ void __launch_bounds__(kBX *kBY)
     k_prolong_correct(T *__restrict__ psi, int Nf, int Pf, const T *__restrict__ ec, int Pc) {
+    pdl_enter();
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= Nf || j >= Nf) return;
@@ -281,6 +286,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 // in a block of 64): nsweeps colour sweeps in one block.
 template <typename T, int OP>
 __global__ void k_coarsest(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int nsweeps, T beta) {
+    pdl_enter();
     int n = N - 1;
     int t = threadIdx.x;
     int i = 1 + t % n, j = 1 + t / n;
@@ -309,6 +315,7 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual_norm(const T *__restrict__ psi, const T *__restrict__ g, int N, int P, double *__restrict__ partials,
                     FinishArgs fin) {
+    pdl_enter();
     __shared__ double sh[32];
     int i0 = 1 + blockIdx.x * kRX;
     int j0 = 1 + blockIdx.y * (kRY * kNormRows) + threadIdx.y;
@@ -334,6 +341,7 @@ template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_assemble_rhs(const double *__restrict__ w, double *__restrict__ g, int N, int P, double h2,
                    double *__restrict__ gpart) {
+    pdl_enter();
     __shared__ double sh[32];
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -357,6 +365,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 // that every stage buffer carries the latest (lagged) walls.
 __global__ void k_thom(const double *__restrict__ psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
                        int profile) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int n = N - 1;
     double m2h2 = -2.0 * (double)N * (double)N;
@@ -398,6 +407,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     k_rhs_stage(const double *__restrict__ psi, const double *__restrict__ in, const double *__restrict__ W0,
                 double *__restrict__ acc, double *__restrict__ out, int N, int P, double inv2h, double nu_invh2,
                 int advect, StageCoef k) {
+    pdl_enter();
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= N || j >= N) return;
@@ -429,6 +439,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     k_monitor(const double *__restrict__ p0, const double *__restrict__ p1, const double *__restrict__ w0,
               const double *__restrict__ w1, int N, int P, double *__restrict__ part, unsigned int *counter,
               DevState *ds, double dt) {
+    pdl_enter();
     __shared__ double sh[32];
     __shared__ bool last;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -473,6 +484,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 }
 
 __global__ void k_zero_walls(double *psi, int N, int P) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t > N) return;
     psi[t] = 0.0;
@@ -497,15 +509,15 @@ cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int
         int n = N / 2;                      // at most this many nodes of one parity per direction
         dim3 grid = grid2(n, (n + 1) / 2, kBX, kSmY);  // two rows per thread
         if (relax)
-            k_smooth_colour<T, 1, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+            (void)launch_pdl(k_smooth_colour<T, 1, true>, grid, blk, 0, s, psi, g, N, P, colour, beta);
         else
-            k_smooth_colour<T, 1, false><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+            (void)launch_pdl(k_smooth_colour<T, 1, false>, grid, blk, 0, s, psi, g, N, P, colour, beta);
     } else {
         dim3 grid = grid2(N / 2, N / 2, kBX, kSmY);  // two rows per thread
         if (relax)
-            k_smooth_colour<T, 0, true><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+            (void)launch_pdl(k_smooth_colour<T, 0, true>, grid, blk, 0, s, psi, g, N, P, colour, beta);
         else
-            k_smooth_colour<T, 0, false><<<grid, blk, 0, s>>>(psi, g, N, P, colour, beta);
+            (void)launch_pdl(k_smooth_colour<T, 0, false>, grid, blk, 0, s, psi, g, N, P, colour, beta);
     }
     return cudaGetLastError();
 }
@@ -516,24 +528,24 @@ cudaError_t launch_residual_restrict(cudaStream_t s, int op, const T *psi, const
     int nc = Nf / 2 - 1;
     dim3 grid((nc + kRT - 1) / kRT, (nc + kRT - 1) / kRT), blk(kRT, kRT);
     if (op == 1)
-        k_residual_restrict<T, 1><<<grid, blk, 0, s>>>(psi, g, Nf, Pf, gc, psic, Pc);
+        (void)launch_pdl(k_residual_restrict<T, 1>, grid, blk, 0, s, psi, g, Nf, Pf, gc, psic, Pc);
     else
-        k_residual_restrict<T, 0><<<grid, blk, 0, s>>>(psi, g, Nf, Pf, gc, psic, Pc);
+        (void)launch_pdl(k_residual_restrict<T, 0>, grid, blk, 0, s, psi, g, Nf, Pf, gc, psic, Pc);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prolong_correct(cudaStream_t s, T *psi, int Nf, int Pf, const T *ec, int Pc) {
-    k_prolong_correct<T><<<grid2(Nf - 1, Nf - 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi, Nf, Pf, ec, Pc);
+    (void)launch_pdl(k_prolong_correct<T>, grid2(Nf - 1, Nf - 1, kBX, kBY), dim3(kBX, kBY), 0, s, psi, Nf, Pf, ec, Pc);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_coarsest(cudaStream_t s, int op, T *psi, const T *g, int N, int P, int nsweeps, T beta) {
     if (op == 1)
-        k_coarsest<T, 1><<<1, 64, 0, s>>>(psi, g, N, P, nsweeps, beta);
+        (void)launch_pdl(k_coarsest<T, 1>, 1, 64, 0, s, psi, g, N, P, nsweeps, beta);
     else
-        k_coarsest<T, 0><<<1, 64, 0, s>>>(psi, g, N, P, nsweeps, beta);
+        (void)launch_pdl(k_coarsest<T, 0>, 1, 64, 0, s, psi, g, N, P, nsweeps, beta);
     return cudaGetLastError();
 }
 
@@ -549,9 +561,9 @@ cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *
                                  FinishArgs fin) {
     dim3 grid(residual_blocks_x(N), (N - 1 + kRY * kNormRows - 1) / (kRY * kNormRows)), blk(kBX, kRY);
     if (op == 1)
-        k_residual_norm<T, 1><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
+        (void)launch_pdl(k_residual_norm<T, 1>, grid, blk, 0, s, psi, g, N, P, partials, fin);
     else
-        k_residual_norm<T, 0><<<grid, blk, 0, s>>>(psi, g, N, P, partials, fin);
+        (void)launch_pdl(k_residual_norm<T, 0>, grid, blk, 0, s, psi, g, N, P, partials, fin);
     return cudaGetLastError();
 }
 
@@ -560,16 +572,16 @@ cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, dou
     double h = 1.0 / N;
     dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
     if (op == 1)
-        k_assemble_rhs<1><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
+        (void)launch_pdl(k_assemble_rhs<1>, grid, blk, 0, s, omega, g, N, P, h * h, gpart);
     else
-        k_assemble_rhs<0><<<grid, blk, 0, s>>>(omega, g, N, P, h * h, gpart);
+        (void)launch_pdl(k_assemble_rhs<0>, grid, blk, 0, s, omega, g, N, P, h * h, gpart);
     return cudaGetLastError();
 }
 
 cudaError_t launch_thom(cudaStream_t s, const double *psi, double *W0, double *Wa, double *Wb, int N, int P, double U,
                         int profile) {
     int n = 4 * (N - 1) + 4;
-    k_thom<<<(n + 255) / 256, 256, 0, s>>>(psi, W0, Wa, Wb, N, P, U, profile);
+    (void)launch_pdl(k_thom, (n + 255) / 256, 256, 0, s, psi, W0, Wa, Wb, N, P, U, profile);
     return cudaGetLastError();
 }
 
@@ -577,8 +589,8 @@ cudaError_t launch_rhs_stage(cudaStream_t s, const double *psi, const double *in
                              double *out, int N, int P, double Re, int advect, StageCoef c) {
     double inv2h = 0.5 * N;
     double nu_invh2 = (double)N * (double)N / Re;
-    k_rhs_stage<<<grid2(N - 1, N - 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi, in, W0, acc, out, N, P, inv2h,
-                                                                         nu_invh2, advect, c);
+    (void)launch_pdl(k_rhs_stage, grid2(N - 1, N - 1, kBX, kBY), dim3(kBX, kBY), 0, s, psi, in, W0, acc, out, N, P,
+                     inv2h, nu_invh2, advect, c);
     return cudaGetLastError();
 }
 
@@ -586,13 +598,13 @@ cudaError_t launch_monitor(cudaStream_t s, const double *psi0, const double *psi
                            const double *w1, int N, int P, double *part, DevState *ds, double dt) {
     // the block counter lives just past the partials
     unsigned int *counter = reinterpret_cast<unsigned int *>(part + 3 * monitor_blocks(N));
-    k_monitor<<<grid2(N + 1, N + 1, kBX, kBY), dim3(kBX, kBY), 0, s>>>(psi0, psi1, w0, w1, N, P, part, counter, ds,
-                                                                       dt);
+    (void)launch_pdl(k_monitor, grid2(N + 1, N + 1, kBX, kBY), dim3(kBX, kBY), 0, s, psi0, psi1, w0, w1, N, P, part,
+                     counter, ds, dt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_zero_walls(cudaStream_t s, double *psi, int N, int P) {
-    k_zero_walls<<<(N + 1 + 255) / 256, 256, 0, s>>>(psi, N, P);
+    (void)launch_pdl(k_zero_walls, (N + 1 + 255) / 256, 256, 0, s, psi, N, P);
     return cudaGetLastError();
 }
 
@@ -626,6 +638,7 @@ __device__ __forceinline__ double sor_value(const double *p, const double *__res
 template <int OP>
 __global__ void __launch_bounds__(1024)
     k_sor_lex(double *psi, const double *__restrict__ g, int N, int P, int nsw, double beta) {
+    pdl_enter();
     extern __shared__ double sor_sp[];
     double *p = sor_sp;
     const size_t nodes = (size_t)(N + 1) * P;
@@ -734,9 +747,9 @@ cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g,
         return op == 1 ? launch_sor_cluster<1>(s, psi, g, N, P, nsw, beta)
                        : launch_sor_cluster<0>(s, psi, g, N, P, nsw, beta);
     if (op == 1)
-        k_sor_lex<1><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
+        (void)launch_pdl(k_sor_lex<1>, 1, 1024, sm, s, psi, g, N, P, nsw, beta);
     else
-        k_sor_lex<0><<<1, 1024, sm, s>>>(psi, g, N, P, nsw, beta);
+        (void)launch_pdl(k_sor_lex<0>, 1, 1024, sm, s, psi, g, N, P, nsw, beta);
     return cudaGetLastError();
 }
 

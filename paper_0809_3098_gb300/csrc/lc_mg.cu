@@ -281,6 +281,7 @@ template <typename T, int OP, int TX, int TY>
 __global__ void __launch_bounds__(512)
     k_down(const T *__restrict__ psi_in, int zero_init, const T *__restrict__ g, T *__restrict__ psi_out, int N,
            int P, T *__restrict__ gc, int Pc, int nu, T beta) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     down_body<T, OP, TX, TY>(blockIdx.x, blockIdx.y, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta, smem_raw);
 }
@@ -375,6 +376,7 @@ __global__ void __launch_bounds__(512)
     k_up(const T *__restrict__ psi_in, const T *__restrict__ g, const T *__restrict__ ec, int Pc,
          T *__restrict__ psi_out, int N, int P, int nu, T beta, double *__restrict__ partials, Correct64 cor,
          FinishArgs fin) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     double acc = up_body<T, OP, TX, TY>(blockIdx.x, blockIdx.y, psi_in, g, ec, Pc, psi_out, N, P, nu, beta,
@@ -590,6 +592,7 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(1024)
     k_coarse(const T *__restrict__ g_in, int Pg, const T *__restrict__ psi_warm, T *__restrict__ psi_out, int Po,
              int N0, int nl, int nu1, int nu2, int nuc, T beta, double *__restrict__ partial, FinishArgs fin) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
     double acc = coarse_body<T, OP>(g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial != nullptr,
@@ -621,7 +624,7 @@ cudaError_t down_t(cudaStream_t s, const T *psi_in, int zero_init, const T *g, T
     size_t sm = down_smem<T, TX, TY>(OP, nu);
     auto kern = k_down<T, OP, TX, TY>;
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
-    kern<<<grid, dim3(kTBX, tile_by(TY)), sm, s>>>(psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
+    (void)launch_pdl(kern, grid, dim3(kTBX, tile_by(TY)), sm, s, psi_in, zero_init, g, psi_out, N, P, gc, Pc, nu, beta);
     return cudaGetLastError();
 }
 
@@ -631,7 +634,8 @@ cudaError_t up_t(cudaStream_t s, const T *psi_in, const T *g, const T *ec, int P
     size_t sm = down_smem<T, TX, TY>(OP, nu);
     auto kern = k_up<T, OP, TX, TY>;
     dim3 grid((N - 1 + TX - 1) / TX, (N - 1 + TY - 1) / TY);
-    kern<<<grid, dim3(kTBX, tile_by(TY)), sm, s>>>(psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials, cor, fin);
+    (void)launch_pdl(kern, grid, dim3(kTBX, tile_by(TY)), sm, s, psi_in, g, ec, Pc, psi_out, N, P, nu, beta, partials,
+                     cor, fin);
     return cudaGetLastError();
 }
 
@@ -642,6 +646,7 @@ cudaError_t up_t(cudaStream_t s, const T *psi_in, const T *g, const T *ec, int P
 template <int OP, int TX, int TY>
 __global__ void __launch_bounds__(512)
     k_down_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int bx, by;
     const BatchCav &cv = cav[batch_locate(r, bx, by)];
@@ -653,6 +658,7 @@ __global__ void __launch_bounds__(512)
 template <int OP, int TX, int TY>
 __global__ void __launch_bounds__(512)
     k_up_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int bx, by;
     const BatchCav &cv = cav[batch_locate(r, bx, by)];
@@ -665,6 +671,7 @@ __global__ void __launch_bounds__(512)
 
 template <int OP>
 __global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, int nu2, int nuc, float beta) {
+    pdl_enter();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const BatchCav &cv = cav[blockIdx.x];
     if (!cv.active) return;
@@ -760,6 +767,7 @@ template <typename T, int OP>
 __global__ void __launch_bounds__(512)
     k_coarse_cluster(const T *__restrict__ g_in, int Pg, T *__restrict__ psi_out, int Po, int nu1, int nu2, int nuc,
                      T beta, ClusterPlan pl) {
+    pdl_enter();
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1011,7 +1019,7 @@ cudaError_t launch_coarse(cudaStream_t s, int op, const T *g_in, int Pg, const T
     size_t sm = coarse_smem_bytes(N0, nl, sizeof(T));
     auto kern = op == 1 ? k_coarse<T, 1> : k_coarse<T, 0>;
     dim3 blk(32, sizeof(T) == 8 ? 16 : 32);
-    kern<<<1, blk, sm, s>>>(g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial, fin);
+    (void)launch_pdl(kern, 1, blk, sm, s, g_in, Pg, psi_warm, psi_out, Po, N0, nl, nu1, nu2, nuc, beta, partial, fin);
     return cudaGetLastError();
 }
 
@@ -1064,13 +1072,15 @@ cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg,
     cfg.blockDim = dim3(32, 16);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = tl_pdl ? 2 : 1;
     if (op == 1) return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 1>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
     return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 0>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
 }
@@ -1109,16 +1119,16 @@ namespace {
 template <int OP, int TX, int TY>
 cudaError_t down_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
                          float beta) {
-    k_down_batch<OP, TX, TY><<<nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
-                                                                                                 beta);
+    (void)launch_pdl(k_down_batch<OP, TX, TY>, nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s,
+                     cav, r, level, nu, beta);
     return cudaGetLastError();
 }
 
 template <int OP, int TX, int TY>
 cudaError_t up_batch_t(cudaStream_t s, BatchCav *cav, const BatchRange *r, int level, int nblocks, int nu,
                        float beta) {
-    k_up_batch<OP, TX, TY><<<nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s>>>(cav, r, level, nu,
-                                                                                               beta);
+    (void)launch_pdl(k_up_batch<OP, TX, TY>, nblocks, dim3(kTBX, tile_by(TY)), down_smem<float, TX, TY>(OP, nu), s, cav,
+                     r, level, nu, beta);
     return cudaGetLastError();
 }
 
@@ -1165,9 +1175,9 @@ cudaError_t launch_up_batch<float>(cudaStream_t s, int shape, int op, BatchCav *
 cudaError_t launch_coarse_batch(cudaStream_t s, int op, BatchCav *cav, int count, int smem, int nu1, int nu2, int nuc,
                                 float beta) {
     if (op == 1)
-        k_coarse_batch<1><<<count, dim3(32, 32), smem, s>>>(cav, nu1, nu2, nuc, beta);
+        (void)launch_pdl(k_coarse_batch<1>, count, dim3(32, 32), smem, s, cav, nu1, nu2, nuc, beta);
     else
-        k_coarse_batch<0><<<count, dim3(32, 32), smem, s>>>(cav, nu1, nu2, nuc, beta);
+        (void)launch_pdl(k_coarse_batch<0>, count, dim3(32, 32), smem, s, cav, nu1, nu2, nuc, beta);
     return cudaGetLastError();
 }
 

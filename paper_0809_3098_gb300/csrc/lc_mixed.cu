@@ -59,6 +59,7 @@ template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual64_to32(const double *__restrict__ psi, const double *__restrict__ g, int N, int P,
                       float *__restrict__ r32, int P32, double *__restrict__ partials, FinishArgs fin) {
+    pdl_enter();
     __shared__ float sh[32];
     int i0 = 1 + blockIdx.x * kRX;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 __global__ void __launch_bounds__(kBX *kBY)
     k_correct64(const float *__restrict__ e, int Pe, double *__restrict__ psi, int P64, float *__restrict__ psi32,
                 int P32, int N) {
+    pdl_enter();
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= N || j >= N) return;
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(kBX *kBY)
                       const double *__restrict__ in64, const double *__restrict__ W0, double *__restrict__ acc,
                       double *__restrict__ out64, float *__restrict__ out32, int N, int P64, int P32, float inv2h,
                       float nu_invh2, int advect, StageCoef k) {
+    pdl_enter();
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= N || j >= N) return;
@@ -127,6 +130,7 @@ struct Walls {
 // Thom's wall vorticity (Eq. (25)) in FP64 from psi64, written to the three
 // FP64 stage buffers and their FP32 shadows.
 __global__ void k_thom_mixed(const double *__restrict__ psi, Walls w, int N, int P64, int P32, double U, int profile) {
+    pdl_enter();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     int n = N - 1;
     double m2h2 = -2.0 * (double)N * (double)N;
@@ -165,6 +169,7 @@ __global__ void k_thom_mixed(const double *__restrict__ psi, Walls w, int N, int
 }
 
 __global__ void k_to32(const double *__restrict__ src, int P64, float *__restrict__ dst, int P32, int N) {
+    pdl_enter();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > N || j > N) return;
@@ -183,6 +188,7 @@ __device__ __forceinline__ int stage_out(int s) { return s == 4 ? 0 : (s & 1 ? 2
 template <bool RHS64>
 __global__ void __launch_bounds__(kBX *kBY)
     k_stage_batch(const BatchCav *cav, const BatchRange *r, int stage, StageCoef k, int advect) {
+    pdl_enter();
     int bx, by;
     const BatchCav &cv = cav[batch_locate(r, bx, by)];
     int N = cv.N, P = cv.P[0];
@@ -237,6 +243,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_assemble_batch(BatchCav *cav, const BatchRange *r, int stage, double *__restrict__ gpart) {
+    pdl_enter();
     __shared__ double sh[32];
     int bx, by;
     int ci = batch_locate(r, bx, by);
@@ -270,6 +277,7 @@ template <int OP>
 __global__ void __launch_bounds__(kBX *kBY)
     k_residual_batch(BatchCav *cav, const BatchRange *r, const BatchRange *rg, double *__restrict__ rpart,
                      const double *__restrict__ gpart, BatchFinish fin) {
+    pdl_enter();
     __shared__ double sh[32];
     __shared__ float shf[32];
     __shared__ unsigned int s_last;
@@ -347,6 +355,7 @@ __global__ void __launch_bounds__(kBX *kBY)
 // FP32 shadow of every cavity's psi64 after its solve (read only by the next
 // stage's FP32 L(omega)).
 __global__ void __launch_bounds__(kBX *kBY) k_psi32_batch(const BatchCav *cav, const BatchRange *r) {
+    pdl_enter();
     int bx, by;
     const BatchCav &cv = cav[batch_locate(r, bx, by)];
     int N = cv.N, P = cv.P[0];
@@ -358,6 +367,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_psi32_batch(const BatchCav *cav, c
 
 // Thom's wall vorticity for every cavity (blockIdx.y = cavity), uniform lid U.
 __global__ void k_thom_batch(const BatchCav *cav, double U) {
+    pdl_enter();
     const BatchCav &cv = cav[blockIdx.y];
     int N = cv.N, P = cv.P[0];
     int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,38 +418,38 @@ cudaError_t launch_stage_batch(cudaStream_t s, BatchCav *cav, const BatchRange *
         {0.178079954393132, 0.821920045606868, 0.544974750228521, 0.096059710526147, 0.063692468666290, 2},
         {0.0, 0.386708617503269, 0.226007483236906, 0.0, 0.0, 3}};
     if (rhs64)
-        k_stage_batch<true><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
+        (void)launch_pdl(k_stage_batch<true>, nblocks, dim3(kBX, kBY), 0, s, cav, r, stage, kc[stage], advect);
     else
-        k_stage_batch<false><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, kc[stage], advect);
+        (void)launch_pdl(k_stage_batch<false>, nblocks, dim3(kBX, kBY), 0, s, cav, r, stage, kc[stage], advect);
     return cudaGetLastError();
 }
 
 cudaError_t launch_assemble_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int nblocks, int stage,
                                   double *gpart) {
     if (op == 1)
-        k_assemble_batch<1><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, gpart);
+        (void)launch_pdl(k_assemble_batch<1>, nblocks, dim3(kBX, kBY), 0, s, cav, r, stage, gpart);
     else
-        k_assemble_batch<0><<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r, stage, gpart);
+        (void)launch_pdl(k_assemble_batch<0>, nblocks, dim3(kBX, kBY), 0, s, cav, r, stage, gpart);
     return cudaGetLastError();
 }
 
 cudaError_t launch_residual_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, const BatchRange *rg,
                                   int nblocks, double *rpart, const double *gpart, BatchFinish fin) {
     if (op == 1)
-        k_residual_batch<1><<<nblocks, dim3(kBX, kRY), 0, s>>>(cav, r, rg, rpart, gpart, fin);
+        (void)launch_pdl(k_residual_batch<1>, nblocks, dim3(kBX, kRY), 0, s, cav, r, rg, rpart, gpart, fin);
     else
-        k_residual_batch<0><<<nblocks, dim3(kBX, kRY), 0, s>>>(cav, r, rg, rpart, gpart, fin);
+        (void)launch_pdl(k_residual_batch<0>, nblocks, dim3(kBX, kRY), 0, s, cav, r, rg, rpart, gpart, fin);
     return cudaGetLastError();
 }
 
 cudaError_t launch_psi32_batch(cudaStream_t s, BatchCav *cav, const BatchRange *r, int nblocks) {
-    k_psi32_batch<<<nblocks, dim3(kBX, kBY), 0, s>>>(cav, r);
+    (void)launch_pdl(k_psi32_batch, nblocks, dim3(kBX, kBY), 0, s, cav, r);
     return cudaGetLastError();
 }
 
 cudaError_t launch_thom_batch(cudaStream_t s, BatchCav *cav, int count, double U) {
     // N <= 8192: 4 (N - 1) + 4 <= 32768 wall nodes
-    k_thom_batch<<<dim3(32768 / 256, count), 256, 0, s>>>(cav, U);
+    (void)launch_pdl(k_thom_batch, dim3(32768 / 256, count), 256, 0, s, cav, U);
     return cudaGetLastError();
 }
 
@@ -447,15 +457,15 @@ cudaError_t launch_residual64_to32(cudaStream_t s, int op, const double *psi64, 
                                    float *r32, int P32, double *partials, FinishArgs fin) {
     dim3 grid(residual_blocks_x(N), (N - 1 + kRY - 1) / kRY);
     if (op == 1)
-        k_residual64_to32<1><<<grid, dim3(kBX, kRY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials, fin);
+        (void)launch_pdl(k_residual64_to32<1>, grid, dim3(kBX, kRY), 0, s, psi64, g64, N, P64, r32, P32, partials, fin);
     else
-        k_residual64_to32<0><<<grid, dim3(kBX, kRY), 0, s>>>(psi64, g64, N, P64, r32, P32, partials, fin);
+        (void)launch_pdl(k_residual64_to32<0>, grid, dim3(kBX, kRY), 0, s, psi64, g64, N, P64, r32, P32, partials, fin);
     return cudaGetLastError();
 }
 
 cudaError_t launch_correct64(cudaStream_t s, const float *e32, int Pe, double *psi64, int P64, float *psi32, int P32,
                              int N) {
-    k_correct64<<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(e32, Pe, psi64, P64, psi32, P32, N);
+    (void)launch_pdl(k_correct64, grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s, e32, Pe, psi64, P64, psi32, P32, N);
     return cudaGetLastError();
 }
 
@@ -464,8 +474,8 @@ cudaError_t launch_rhs_stage_mixed(cudaStream_t s, const float *psi32, int Ps, c
                                    double Re, int advect, StageCoef c) {
     float inv2h = (float)(0.5 * N);
     float nu_invh2 = (float)((double)N * (double)N / Re);
-    k_rhs_stage_mixed<<<grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s>>>(psi32, Ps, in32, in64, W0, acc, out64, out32, N,
-                                                                      P64, P32, inv2h, nu_invh2, advect, c);
+    (void)launch_pdl(k_rhs_stage_mixed, grid2(N - 1, N - 1), dim3(kBX, kBY), 0, s, psi32, Ps, in32, in64, W0, acc,
+                     out64, out32, N, P64, P32, inv2h, nu_invh2, advect, c);
     return cudaGetLastError();
 }
 
@@ -477,12 +487,12 @@ cudaError_t launch_thom_mixed(cudaStream_t s, const double *psi64, double *const
         w.w32[b] = w32[b];
     }
     int n = 4 * (N - 1) + 4;
-    k_thom_mixed<<<(n + 255) / 256, 256, 0, s>>>(psi64, w, N, P64, P32, U, profile);
+    (void)launch_pdl(k_thom_mixed, (n + 255) / 256, 256, 0, s, psi64, w, N, P64, P32, U, profile);
     return cudaGetLastError();
 }
 
 cudaError_t launch_to32(cudaStream_t s, const double *src, int P64, float *dst, int P32, int N) {
-    k_to32<<<grid2(N + 1, N + 1), dim3(kBX, kBY), 0, s>>>(src, P64, dst, P32, N);
+    (void)launch_pdl(k_to32, grid2(N + 1, N + 1), dim3(kBX, kBY), 0, s, src, P64, dst, P32, N);
     return cudaGetLastError();
 }
 

@@ -341,6 +341,7 @@ template <int OP>
 __global__ void __launch_bounds__(32 * kWarps)
     k_down_w(const float *__restrict__ g, float *__restrict__ e_out, int N, int P, float *__restrict__ gc, int Pc,
              int nu, float beta) {
+    pdl_enter();
     int tx, ty;
     if (!wtile_of(N, blockIdx.x * kWarps + (threadIdx.x >> 5), tx, ty)) return;  // whole warps leave
     wdown<OP>(wtile(N, P, tx, ty, OP, nu), g, e_out, gc, Pc, nu, beta);
@@ -350,6 +351,7 @@ template <int OP>
 __global__ void __launch_bounds__(32 * kWarps)
     k_up_w(const float *__restrict__ e_in, const float *__restrict__ g, const float *__restrict__ ec, int Pc,
            float *__restrict__ e_out, int N, int P, int nu, float beta, Correct64 cor) {
+    pdl_enter();
     int tx, ty;
     if (!wtile_of(N, blockIdx.x * kWarps + (threadIdx.x >> 5), tx, ty)) return;
     wup<OP>(wtile(N, P, tx, ty, OP, nu), e_in, g, ec, Pc, e_out, nu, beta, cor);
@@ -371,6 +373,7 @@ __device__ __forceinline__ int wlocate(const BatchRange *r, int &local) {
 template <int OP>
 __global__ void __launch_bounds__(32 * kWarps)
     k_down_w_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    pdl_enter();
     int local;
     const BatchCav &cv = cav[wlocate(r, local)];
     if (!cv.active) return;
@@ -383,6 +386,7 @@ __global__ void __launch_bounds__(32 * kWarps)
 template <int OP>
 __global__ void __launch_bounds__(32 * kWarps)
     k_up_w_batch(BatchCav *cav, const BatchRange *r, int level, int nu, float beta) {
+    pdl_enter();
     int local;
     const BatchCav &cv = cav[wlocate(r, local)];
     if (!cv.active) return;
@@ -405,36 +409,38 @@ int warp_tile_blocks(int N) {
 cudaError_t launch_down_warp(cudaStream_t s, int op, const float *g, float *e_out, int N, int P, float *gc, int Pc,
                              int nu, float beta) {
     if (op == 1)
-        k_down_w<1><<<warp_tile_blocks(N), 32 * kWarps, 0, s>>>(g, e_out, N, P, gc, Pc, nu, beta);
+        (void)launch_pdl(k_down_w<1>, warp_tile_blocks(N), 32 * kWarps, 0, s, g, e_out, N, P, gc, Pc, nu, beta);
     else
-        k_down_w<0><<<warp_tile_blocks(N), 32 * kWarps, 0, s>>>(g, e_out, N, P, gc, Pc, nu, beta);
+        (void)launch_pdl(k_down_w<0>, warp_tile_blocks(N), 32 * kWarps, 0, s, g, e_out, N, P, gc, Pc, nu, beta);
     return cudaGetLastError();
 }
 
 cudaError_t launch_up_warp(cudaStream_t s, int op, const float *e_in, const float *g, const float *ec, int Pc,
                            float *e_out, int N, int P, int nu, float beta, Correct64 cor) {
     if (op == 1)
-        k_up_w<1><<<warp_tile_blocks(N), 32 * kWarps, 0, s>>>(e_in, g, ec, Pc, e_out, N, P, nu, beta, cor);
+        (void)launch_pdl(k_up_w<1>, warp_tile_blocks(N), 32 * kWarps, 0, s, e_in, g, ec, Pc, e_out, N, P, nu, beta,
+                         cor);
     else
-        k_up_w<0><<<warp_tile_blocks(N), 32 * kWarps, 0, s>>>(e_in, g, ec, Pc, e_out, N, P, nu, beta, cor);
+        (void)launch_pdl(k_up_w<0>, warp_tile_blocks(N), 32 * kWarps, 0, s, e_in, g, ec, Pc, e_out, N, P, nu, beta,
+                         cor);
     return cudaGetLastError();
 }
 
 cudaError_t launch_down_warp_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int level, int nblocks,
                                    int nu, float beta) {
     if (op == 1)
-        k_down_w_batch<1><<<nblocks, 32 * kWarps, 0, s>>>(cav, r, level, nu, beta);
+        (void)launch_pdl(k_down_w_batch<1>, nblocks, 32 * kWarps, 0, s, cav, r, level, nu, beta);
     else
-        k_down_w_batch<0><<<nblocks, 32 * kWarps, 0, s>>>(cav, r, level, nu, beta);
+        (void)launch_pdl(k_down_w_batch<0>, nblocks, 32 * kWarps, 0, s, cav, r, level, nu, beta);
     return cudaGetLastError();
 }
 
 cudaError_t launch_up_warp_batch(cudaStream_t s, int op, BatchCav *cav, const BatchRange *r, int level, int nblocks,
                                  int nu, float beta) {
     if (op == 1)
-        k_up_w_batch<1><<<nblocks, 32 * kWarps, 0, s>>>(cav, r, level, nu, beta);
+        (void)launch_pdl(k_up_w_batch<1>, nblocks, 32 * kWarps, 0, s, cav, r, level, nu, beta);
     else
-        k_up_w_batch<0><<<nblocks, 32 * kWarps, 0, s>>>(cav, r, level, nu, beta);
+        (void)launch_pdl(k_up_w_batch<0>, nblocks, 32 * kWarps, 0, s, cav, r, level, nu, beta);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,20 @@ def test_batch_eager_equals_graph_and_autotune_keeps_bits():
         assert np.array_equal(a.cycle_log(c), t.cycle_log(c))
 
 
+@pytest.mark.parametrize("graph", [0, 1])
+def test_batch_pdl_bitwise_equals_plain_launches(graph):
+    """Programmatic dependent launch (the default) against plain stream order,
+    in the step graph and eagerly."""
+    Ns, Res = [256, 128, 384], [5000.0, 800.0, 20000.0]
+    a = lc.Batch(Ns, Res, graph=graph)
+    b = lc.Batch(Ns, Res, graph=graph, pdl=0)
+    a.step(2)
+    b.step(2)
+    for c in range(3):
+        assert np.array_equal(a.cycle_log(c), b.cycle_log(c))
+        assert np.array_equal(a.psi(c), b.psi(c)) and np.array_equal(a.omega(c), b.omega(c))
+
+
 def test_schedule_autotuner_restores_state_and_sets_schedule():
     """After the schedule search the batch is back at its starting state and
     steps exactly like a fresh batch given the chosen (nu1, nu2)."""

@@ -144,3 +144,15 @@ def test_mixed_cluster_coarse_bitwise_identical(N, op):
     for p, w, cyc in runs[1:]:
         assert np.array_equal(cyc, runs[0][2])
         assert np.array_equal(p, runs[0][0]) and np.array_equal(w, runs[0][1])
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_mixed_pdl_bitwise_identical(graph):
+    """Programmatic dependent launch (default) against plain stream order."""
+    out = []
+    for pdl in (0, 1):
+        g = lc.Cavity(512, 10000.0, precision=MIXED, pdl=pdl, graph=graph)
+        g.step(2)
+        out.append((g.psi(), g.omega(), g.cycle_log()))
+    assert np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])

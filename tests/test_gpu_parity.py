@@ -225,6 +225,11 @@ MODES = {
     "cluster3-split8": dict(blocked=1, fine_phases=0, coarse_cluster=3, cluster_max=64, cluster_split=8),
     "cluster5-split4": dict(blocked=1, fine_phases=1, coarse_cluster=5, cluster_max=512, cluster_split=4),
     "cluster8-split32": dict(blocked=1, fine_phases=1, coarse_cluster=8, cluster_split=32),
+    # kernels launched one after another instead of with programmatic
+    # dependent launch (the default): the same kernels and values
+    "no-pdl": dict(pdl=0),
+    "no-pdl-eager": dict(pdl=0, graph=0),
+    "pdl-eager": dict(graph=0),
 }
 
 
