@@ -140,8 +140,12 @@ const char *lc_last_error(void);
  *                 memory tile kernels (all colour phases of a level's smoothing
  *                 in one launch, halos recomputed); 0: one launch per colour
  *                 phase on every level.  FP64 only; results are identical.
- *   "fine_phases" 1 (default): with "blocked", the finest FP64 level still
- *                 uses one launch per colour phase (no recomputed halo).
+ *   "fine_phases" FP64 with "blocked": the number of finest levels that run
+ *                 as one launch per colour phase (no recomputed halo); the
+ *                 levels between them and the coarse V-cycle run as tile
+ *                 kernels.  Default 16: every level above the coarse one (on
+ *                 GB300 the tiles' recomputed FP64 halo costs more than the
+ *                 extra launches), 0..16.
  *   "coarse_max"  levels with at most this many intervals run as one V-cycle
  *                 in a single thread block (default -1: 32 for FP64, 64 for
  *                 mixed precision), 2..256; used where the cluster form below

@@ -156,7 +156,8 @@ struct lc_ctx {
     int fused = 0;                 // 1: fine-level FP64 colour phases of a pass in one cooperative launch
     int barrier_extra = 0;         // test hook: the fused kernel's barrier waits for this many more blocks
     int fused_blocks[2] = {0, 0};  // its grid (beta == 1, beta != 1); 0: not available
-    int blocked = 1, fine_phases = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
+    int blocked = 1, coarse_max = -1;  // -1: 32 (FP64) or 64 (mixed)
+    int fine_phases = kMaxLevels;     // FP64: levels above the coarse one with one launch per colour phase
     int tile_force = -1;                                // >= 0: one tile shape on every level
     int coarse_cluster = -1;  // coarse V-cycle on a cluster of this many blocks; -1: auto (FP64), 0: off
     int cluster_max = -1;     // first level run by the cluster kernel: N_l <= cluster_max (-1: 128)
@@ -310,6 +311,20 @@ int enqueue_fine_sweeps(lc_ctx *c, cudaStream_t s, int nsw) {
     return k;
 }
 
+// nsw smoothing sweeps of level l with one launch per colour phase (the fine
+// level may take the fused form); returns the launch count or an error code.
+int level_sweeps(lc_ctx *c, cudaStream_t s, int l, int nsw) {
+    if (l == 0) return enqueue_fine_sweeps(c, s, nsw);
+    const Layout &L = c->lay;
+    int nc = c->op == LC_OP_COMPACT ? 4 : 2, k = 0;
+    for (int sw = 0; sw < nsw; ++sw)
+        for (int col = 0; col < nc; ++col, ++k) {
+            cudaError_t e = launch_smooth_colour<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], col, c->beta);
+            if (e != cudaSuccess) return cuda_fail(e, "launch_smooth_colour");
+        }
+    return k;
+}
+
 FinishArgs finish_args(const lc_ctx *c, int nr, cudaGraphConditionalHandle h) {
     const Layout &L = c->lay;
     return FinishArgs{1, nr, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol, c->max_cycles};
@@ -325,16 +340,16 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
     if (!blocked_ok(c)) return enqueue_vcycle_phases(c, s);
     const Layout &L = c->lay;
     int lc = coarse_level(c);
-    bool phases0 = c->fine_phases && lc > 0;
+    const int nph = c->fine_phases < lc ? c->fine_phases : lc;  // finest levels with one launch per phase
     double *rpart = c->at<double>(L.rpart);
     int k = 0;
     for (int l = 0; l < lc; ++l) {
-        if (l == 0 && phases0) {
-            int n = enqueue_fine_sweeps(c, s, c->nu1);
+        if (l < nph) {
+            int n = level_sweeps(c, s, l, c->nu1);
             if (n < 0) return n;
             k += n;
-            LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], c->g(1),
-                                                     c->psi(1), L.Pl[1]));
+            LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], c->g(l + 1),
+                                                     c->psi(l + 1), L.Pl[l + 1]));
         } else {
             LC_CUDA(launch_down<double>(s, tile_shape(c, l), c->op, c->psi(l), l > 0, c->g(l), c->psiB(l), L.Nl[l],
                                         L.Pl[l], c->g(l + 1), L.Pl[l + 1], c->nu1, c->beta));
@@ -352,9 +367,9 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
     ++k;
     Correct64 none{nullptr, 0, nullptr, 0};
     for (int l = lc - 1; l >= 0; --l) {
-        if (l == 0 && phases0) {
-            LC_CUDA(launch_prolong_correct<double>(s, c->psi(0), L.Nl[0], L.Pl[0], c->psi(1), L.Pl[1]));
-            int n = enqueue_fine_sweeps(c, s, c->nu2);
+        if (l < nph) {
+            LC_CUDA(launch_prolong_correct<double>(s, c->psi(l), L.Nl[l], L.Pl[l], c->psi(l + 1), L.Pl[l + 1]));
+            int n = level_sweeps(c, s, l, c->nu2);
             if (n < 0) return n;
             k += n;
         } else {
@@ -364,7 +379,7 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
         }
         ++k;
     }
-    *norm_done = lc == 0 || !phases0;
+    *norm_done = lc == 0 || nph == 0;
     c->kernels_per_cycle = k;
     return LC_OK;
 }
@@ -806,9 +821,12 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
     } else if (k == "advect") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "advect must be 0 or 1");
         c->advect = iv;
-    } else if (k == "blocked" || k == "fine_phases") {
+    } else if (k == "fine_phases") {
+        if (!integral || iv < 0 || iv > kMaxLevels) return fail(LC_ERR_ARG, "fine_phases must be 0..16");
+        c->fine_phases = iv;
+    } else if (k == "blocked") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, k + " must be 0 or 1");
-        (k == "blocked" ? c->blocked : c->fine_phases) = iv;
+        c->blocked = iv;
     } else if (k == "tile_shape") {
         if (!integral || iv < -1 || iv > 4) return fail(LC_ERR_ARG, "tile_shape must be -1 (auto) or 0..4");
         c->tile_force = iv;

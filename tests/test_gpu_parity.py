@@ -227,6 +227,8 @@ MODES = {
     "cluster8-split32": dict(blocked=1, fine_phases=1, coarse_cluster=8, cluster_split=32),
     # kernels launched one after another instead of with programmatic
     # dependent launch (the default): the same kernels and values
+    "phases-2-levels": dict(fine_phases=2),
+    "phases-3-levels-no-cluster": dict(fine_phases=3, **NOCL),
     "no-pdl": dict(pdl=0),
     "no-pdl-eager": dict(pdl=0, graph=0),
     "pdl-eager": dict(graph=0),
