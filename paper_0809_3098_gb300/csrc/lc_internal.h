@@ -169,6 +169,29 @@ __device__ __forceinline__ bool rho_halo(const T *__restrict__ psi, const T *__r
     return true;
 }
 
+// rho = GS - psi at node c of an array with row pitch P, for the residuals
+// that feed a restriction or a norm.  In FP64 the compact operator takes the
+// H-form of rho_halo with the column sums formed at the node (same operands,
+// order and rounding, so every FP64 residual of the library agrees bit for
+// bit with rho_halo's); FP32, whose V-cycle kernels share the GS form, and
+// the 5-point operator (where the two forms coincide) take GS - psi.
+template <typename T, int OP, typename I>
+__device__ __forceinline__ T rho_node(const T *p, const T *g, I c, int P) {
+    if constexpr (OP == 1 && sizeof(T) == 8) {
+        T V = p[c + P] + p[c - P];
+        T Hr = fma(T(4), p[c + 1], p[c + 1 + P] + p[c + 1 - P]);
+        T Hl = fma(T(4), p[c - 1], p[c - 1 + P] + p[c - 1 - P]);
+        return fma(T(0.05), fma(T(4), V, Hr + Hl), g[c] - p[c]);
+    } else {
+        T n4 = (p[c + 1] + p[c - 1]) + (p[c + P] + p[c - P]);
+        if (OP == 1) {
+            T d4 = (p[c + P + 1] + p[c - P + 1]) + (p[c + P - 1] + p[c - P - 1]);
+            return fma(T(0.2), n4, fma(T(0.05), d4, g[c])) - p[c];
+        }
+        return fma(T(0.25), n4, g[c]) - p[c];
+    }
+}
+
 __device__ __forceinline__ double finish_block_sum(double v, double *sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int t = threadIdx.y * blockDim.x + threadIdx.x;

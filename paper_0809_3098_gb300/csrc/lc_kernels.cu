@@ -233,20 +233,52 @@ __global__ void __launch_bounds__(kRT *kRT)
     k_residual_restrict(const T *__restrict__ psi, const T *__restrict__ g, int Nf, int Pf, T *__restrict__ gc,
                         T *__restrict__ psic, int Pc) {
     pdl_enter();
-    __shared__ T rho[2 * kRT + 1][2 * kRT + 2];
+    constexpr int kW = 2 * kRT + 1;  // the fine patch is kW x kW nodes
+    __shared__ T rho[kW][kW + 1];
     int Nc = Nf / 2;
     int I0 = 1 + blockIdx.x * kRT, J0 = 1 + blockIdx.y * kRT;
     int fi0 = 2 * I0 - 1, fj0 = 2 * J0 - 1;
     int t = threadIdx.y * kRT + threadIdx.x;
-    for (int k = t; k < (2 * kRT + 1) * (2 * kRT + 1); k += kRT * kRT) {
-        int x = k % (2 * kRT + 1), y = k / (2 * kRT + 1);
-        int i = fi0 + x, j = fj0 + y;
-        T r = T(0);
-        if (i >= 1 && i < Nf && j >= 1 && j < Nf) {
-            size_t c = (size_t)j * Pf + i;
-            r = gs_value<T, OP>(psi, g, c, Pf) - psi[c];
+    if constexpr (OP == 1 && sizeof(T) == 8) {
+        // rho_node's H-form with each column sum V and H = 4 psi + V formed
+        // once per node of the patch (plus one column on each side) and
+        // shared by the three residuals that use it: six FP64 operations per
+        // node instead of nine, the same values
+        __shared__ T sV[kW][kW + 2], sH[kW][kW + 2];
+        for (int k = t; k < kW * (kW + 2); k += kRT * kRT) {
+            int x = k % (kW + 2), y = k / (kW + 2);
+            int i = fi0 - 1 + x, j = fj0 + y;
+            T V = T(0), H = T(0);
+            if (i <= Nf && j < Nf) {
+                size_t c = (size_t)j * Pf + i;
+                V = psi[c + Pf] + psi[c - Pf];
+                H = fma(T(4), psi[c], V);
+            }
+            sV[y][x] = V;
+            sH[y][x] = H;
         }
-        rho[y][x] = r;
+        __syncthreads();
+        for (int k = t; k < kW * kW; k += kRT * kRT) {
+            int x = k % kW, y = k / kW;
+            int i = fi0 + x, j = fj0 + y;
+            T r = T(0);
+            if (i < Nf && j < Nf) {
+                size_t c = (size_t)j * Pf + i;
+                r = fma(T(0.05), fma(T(4), sV[y][x + 1], sH[y][x + 2] + sH[y][x]), g[c] - psi[c]);
+            }
+            rho[y][x] = r;
+        }
+    } else {
+        for (int k = t; k < kW * kW; k += kRT * kRT) {
+            int x = k % kW, y = k / kW;
+            int i = fi0 + x, j = fj0 + y;
+            T r = T(0);
+            if (i >= 1 && i < Nf && j >= 1 && j < Nf) {
+                size_t c = (size_t)j * Pf + i;
+                r = rho_node<T, OP>(psi, g, c, Pf);
+            }
+            rho[y][x] = r;
+        }
     }
     __syncthreads();
     int I = I0 + threadIdx.x, J = J0 + threadIdx.y;

@@ -257,7 +257,7 @@ __device__ __forceinline__ void down_body(int bx, int by, const T *__restrict__ 
             int c = y * LP + x;
             bool interior = gi >= 1 && gi < N && gj >= 1 && gj < N;
             if (interior && x < RX + TX && y < RY + TY) psi_out[(size_t)gj * P + gi] = sp[c];
-            sg[c] = interior ? gs_local<T, OP>(sp, sg, c, LP) - sp[c] : T(0);
+            sg[c] = interior ? rho_node<T, OP>(sp, sg, c, LP) : T(0);
         }
     }
     __syncthreads();
@@ -363,7 +363,7 @@ __device__ __forceinline__ double up_body(int bx, int by, const T *__restrict__ 
                 psi_out[(size_t)gj * P + gi] = sp[c];
             }
             if (want_norm) {
-                double r = (double)(gs_local<T, OP>(sp, sg, c, LP) - sp[c]);
+                double r = (double)rho_node<T, OP>(sp, sg, c, LP);
                 acc += r * r;
             }
         }
@@ -503,7 +503,7 @@ __device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int 
             for (unsigned q = tid; q < m * m; q += nt) {
                 const unsigned yy = q / m;
                 const int c = (1 + (int)yy) * LP + 1 + (int)(q - yy * m);
-                sr[c] = gs_local<T, OP>(sp, sg, c, LP) - sp[c];
+                sr[c] = rho_node<T, OP>(sp, sg, c, LP);
             }
             for (int q = tid; q < 4 * n; q += nt) {  // the boundary ring
                 const int side = q / n, k = q - side * n;
@@ -519,7 +519,7 @@ __device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int 
             for (int y = ty; y <= n; y += by)
                 for (int x = tx; x <= n; x += bx) {
                     int q = y * LP + x;
-                    sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? gs_local<T, OP>(sp, sg, q, LP) - sp[q] : T(0);
+                    sr[q] = (x >= 1 && x < n && y >= 1 && y < n) ? rho_node<T, OP>(sp, sg, q, LP) : T(0);
                 }
             __syncthreads();
             for (int Y = 1 + ty; Y < nc; Y += by)
@@ -581,7 +581,7 @@ __device__ __forceinline__ double coarse_body(const T *__restrict__ g_in, int Pg
             int q = y * L0 + x;
             psi_out[(size_t)y * Po + x] = base[q];
             if (want_norm) {
-                double r = (double)(gs_local<T, OP>(base, base + L0 * L0, q, L0) - base[q]);
+                double r = (double)rho_node<T, OP>(base, base + L0 * L0, q, L0);
                 acc += r * r;
             }
         }
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(512)
             for (int y = st.lo + ty; y < st.hi; y += by) {
                 const T *row = ps + (y - st.lo + 1) * LP, *grow = gs + (y - st.lo) * LP;
                 T *rrow = rs + (y - st.lo) * LP;
-                for (int x = 1 + tx; x <= m; x += bx) rrow[x] = gs_local<T, OP>(row, grow, x, LP) - row[x];
+                for (int x = 1 + tx; x <= m; x += bx) rrow[x] = rho_node<T, OP>(row, grow, x, LP);
             }
         cl.sync();
         // full weighting of the residual rows 2Y - 1, 2Y, 2Y + 1 (owned by any block)
