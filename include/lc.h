@@ -118,12 +118,15 @@ const char *lc_last_error(void);
  *                 n / n+1 superscripts fix (i outer, j inner), a "cycle" being
  *                 sor_sweeps sweeps followed by the stopping test.  FP64 only.
  *   "sor_sweeps"  sweeps per SOR cycle (16), 1..4096
- *   "fused"       0 (default): one launch per fine-level FP64 colour phase;
- *                 1: the colour phases of one smoothing pass run as one
- *                 cooperative launch with a bounded grid barrier between
- *                 phases (same values; LC_ERR_TIMEOUT if a barrier wait gave
- *                 up).  On GB300 the barrier costs about what a launch does,
- *                 so the default is 0.
+ *   "fused"       bit mask, 0 (default): one launch per FP64 colour phase;
+ *                 bit 0 (1): the fine level's colour phases of one smoothing
+ *                 pass run as one cooperative launch with a bounded grid
+ *                 barrier between phases; bit 1 (2): the same on the coarser
+ *                 phase levels, with as few blocks as their rows need (same
+ *                 values; LC_ERR_TIMEOUT if a barrier wait gave up).  On GB300
+ *                 a grid barrier costs more than a launch in the step graph
+ *                 (1024^2: 8.3 ms per step with 0, 9.5 with 2), so the
+ *                 default is 0.
  *   "barrier_extra" test hook (0 default): 1 makes the fused smoother's grid
  *                 barrier wait for one block more than the launch has, so
  *                 every wait runs out (about 0.2 s each) and the next

@@ -295,7 +295,7 @@ int enqueue_vcycle_phases(lc_ctx *c, cudaStream_t s) {
 // negative error code.
 int enqueue_fine_sweeps(lc_ctx *c, cudaStream_t s, int nsw) {
     const Layout &L = c->lay;
-    int nb = c->fused ? c->fused_blocks[c->beta != 1.0 ? 1 : 0] : 0;
+    int nb = (c->fused & 1) ? c->fused_blocks[c->beta != 1.0 ? 1 : 0] : 0;
     if (nb > 0) {
         cudaError_t e = launch_smooth_fused<double>(s, c->op, c->psi(0), c->g(0), L.Nl[0], L.Pl[0], nsw, c->beta,
                                                     c->ds(), nb, c->barrier_extra);
@@ -316,6 +316,14 @@ int enqueue_fine_sweeps(lc_ctx *c, cudaStream_t s, int nsw) {
 int level_sweeps(lc_ctx *c, cudaStream_t s, int l, int nsw) {
     if (l == 0) return enqueue_fine_sweeps(c, s, nsw);
     const Layout &L = c->lay;
+    int nmax = (c->fused & 2) ? c->fused_blocks[c->beta != 1.0 ? 1 : 0] : 0;
+    if (nmax > 0) {  // one cooperative launch, as few blocks as the level's rows need
+        cudaError_t e = launch_smooth_fused<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], nsw, c->beta,
+                                                    c->ds(), smooth_fused_level_blocks(c->op, L.Nl[l], nmax),
+                                                    c->barrier_extra);
+        if (e != cudaSuccess) return cuda_fail(e, "launch_smooth_fused");
+        return 1;
+    }
     int nc = c->op == LC_OP_COMPACT ? 4 : 2, k = 0;
     for (int sw = 0; sw < nsw; ++sw)
         for (int col = 0; col < nc; ++col, ++k) {
@@ -798,7 +806,7 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "barrier_extra must be 0 or 1");
         c->barrier_extra = iv;
     } else if (k == "fused") {
-        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "fused must be 0 or 1");
+        if (!integral || iv < 0 || iv > 3) return fail(LC_ERR_ARG, "fused must be 0..3");
         c->fused = iv;
     } else if (k == "sor_sweeps") {
         if (!integral || iv < 1 || iv > 4096) return fail(LC_ERR_ARG, "sor_sweeps must be 1..4096");

@@ -294,6 +294,9 @@ cudaError_t launch_smooth_fused(cudaStream_t s, int op, T *psi, const T *g, int 
 // Co-resident blocks of the fused smoother on the current device (0 if the
 // device cannot launch cooperative kernels).
 int smooth_fused_blocks(int op, bool relax);
+// Blocks of the fused smoother for a level of N intervals: one warp-sized
+// item per warp, at most nmax (the co-resident limit).
+int smooth_fused_level_blocks(int op, int N, int nmax);
 // nsw lexicographic SOR sweeps (Eq. (15) in its superscripts' order) in one
 // block, pipelined over wavefronts; psi in shared memory when
 // sor_smem_bytes(N, P) <= kMaxSmem.

@@ -824,6 +824,13 @@ cudaError_t launch_smooth_fused(cudaStream_t s, int op, T *psi, const T *g, int 
 template cudaError_t launch_smooth_fused<double>(cudaStream_t, int, double *, const double *, int, int, int, double,
                                                  DevState *, int, int);
 
+int smooth_fused_level_blocks(int op, int N, int nmax) {
+    const int na = N / 2, nb = op == 1 ? (N / 2 + 1) / 2 : N / 2;
+    const int items = ((na + 31) / 32) * nb;  // warp-sized items of k_smooth_fused
+    const int want = (items + 7) / 8;         // one item per warp of a 256-thread block
+    return want < 1 ? 1 : (want < nmax ? want : nmax);
+}
+
 int smooth_fused_blocks(int op, bool relax) {
     int dev = 0, coop = 0, sms = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;

@@ -228,6 +228,8 @@ MODES = {
     # kernels launched one after another instead of with programmatic
     # dependent launch (the default): the same kernels and values
     "phases-2-levels": dict(fine_phases=2),
+    "fused-coarser-levels": dict(fused=2),
+    "fused-all-levels": dict(fused=3),
     "phases-3-levels-no-cluster": dict(fine_phases=3, **NOCL),
     "no-pdl": dict(pdl=0),
     "no-pdl-eager": dict(pdl=0, graph=0),
