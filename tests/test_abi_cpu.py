@@ -72,6 +72,14 @@ def test_options_validate_without_gpu(L):
     assert lc.lc_set_option(h, "op", 2) == lc.LC_ERR_ARG
     assert lc.lc_set_option(h, "nonsense", 1) == lc.LC_ERR_ARG
     assert "unknown option" in lc.last_error()
+    # execution options: ranges are checked before any device work
+    for key, ok, bad in (("coarse_cluster", (-1, 0, 2, 16), (1, 17, 0.5)), ("cluster_max", (8, 128, 512), (7, 513)),
+                         ("cluster_split", (4, 16, 256), (3, 257)), ("pdl", (0, 1), (2, -1)),
+                         ("fused", (0, 1, 2, 3), (4, -1)), ("fine_phases", (0, 1, 16), (-1, 17))):
+        for v in ok:
+            assert lc.lc_set_option(h, key, v) == lc.LC_OK, (key, v)
+        for v in bad:
+            assert lc.lc_set_option(h, key, v) == lc.LC_ERR_ARG, (key, v)
     lc.lc_destroy(h)
     assert lc.lc_set_option(h, "nu1", 2) == lc.LC_ERR_ARG  # destroyed
     assert lc.lc_step(0, 1) == lc.LC_ERR_ARG
