@@ -255,6 +255,17 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * change the state: use only on a context whose state no longer matters. */
 int lc_bench_kernel(lc_ctx *ctx, int kernel, int reps, double out[4]);
 
+/* Self-test of the library's FP64 -> FP32 (round to nearest even) and
+ * FP32 -> FP64 conversions done with integer instructions (the step's
+ * mixed-precision kernels use them instead of the hardware conversions, which
+ * on GB300 run on the FP64 unit): on the current device, n >= 0 generated
+ * values (fixed edge cases, then seeded patterns: raw words, the FP32
+ * exponent range, rounding ties, subnormal results) are converted both ways
+ * and compared bit for bit with the hardware conversions (two NaNs compare
+ * equal).  mismatches[0] / [1]: FP64 -> FP32 / FP32 -> FP64 mismatches.
+ * Allocates 16 bytes of device memory for the duration of the call. */
+int lc_selftest_conversions(long long n, unsigned long long seed, long long mismatches[2]);
+
 /* ---- Batched engine ------------------------------------------------------
  * Many cavities of different sizes and Reynolds numbers advanced together:
  * each step is one CUDA graph launch whose kernels cover every cavity (a

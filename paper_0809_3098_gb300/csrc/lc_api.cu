@@ -996,6 +996,26 @@ int lc_get_params(lc_ctx *c, double out[7]) {
     return LC_OK;
 }
 
+int lc_selftest_conversions(long long n, unsigned long long seed, long long mismatches[2]) {
+    if (n < 0 || !mismatches) return fail(LC_ERR_ARG, "n must be >= 0 and mismatches non-NULL");
+    int dev = 0;
+    LC_CUDA(cudaGetDevice(&dev));
+    cudaStream_t s;
+    LC_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    unsigned long long *bad = nullptr, h[2] = {0, 0};
+    cudaError_t e = cudaMalloc(&bad, sizeof(h));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(h), s);
+    if (e == cudaSuccess) e = launch_selftest_conversions(s, n, seed, bad);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, bad, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (bad) cudaFree(bad);
+    cudaStreamDestroy(s);
+    if (e != cudaSuccess) return cuda_fail(e, "lc_selftest_conversions");
+    mismatches[0] = (long long)h[0];
+    mismatches[1] = (long long)h[1];
+    return LC_OK;
+}
+
 int lc_launch_stats(lc_ctx *c, double out[2]) {
     LC_CHECK_CTX(c);
     if (!out) return fail(LC_ERR_ARG, "NULL output");

@@ -126,6 +126,62 @@ struct FinishArgs {
 };
 
 #ifdef __CUDACC__
+// FP64 <-> FP32 conversions on the integer pipes.  On GB300 the hardware
+// conversions run on the FP64 unit (~64 clocks per warp instruction, about 2
+// lane conversions per clock per SM, the rate of a DADD), so in kernels
+// bound by that unit they cost as much as the arithmetic.  These give the
+// hardware's bits with integer instructions: f64_to_f32 rounds to nearest,
+// ties to even, with the same overflow to infinity and the same subnormal
+// results; f32_to_f64 is exact.  NaN in gives a NaN (payload not kept).
+// lc_selftest_conversions compares both with the hardware conversions.
+__device__ __forceinline__ float f64_to_f32(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    const unsigned sign = hi & 0x80000000u;
+    const int e = (int)((hi >> 20) & 0x7ffu);
+    if (e == 0x7ff) return __uint_as_float(sign | (((hi & 0xfffffu) | lo) ? 0x7fc00000u : 0x7f800000u));
+    const int E = e - 896;  // exponent field of the float: 1023 - 127 = 896
+    if (E >= 255) return __uint_as_float(sign | 0x7f800000u);
+    if (E >= 1) {  // normal result: top 23 of the 52 mantissa bits, round on the other 29
+        const unsigned m23 = ((hi & 0xfffffu) << 3) | (lo >> 29), rem = lo & 0x1fffffffu;
+        const unsigned up = rem > 0x10000000u || (rem == 0x10000000u && (m23 & 1u));
+        return __uint_as_float(sign | ((((unsigned)E << 23) | m23) + up));  // a carry moves into the exponent
+    }
+    // subnormal or zero result: the value is m53 2^(e - 1075), the result k 2^-149
+    if (e == 0) return __uint_as_float(sign);  // an FP64 subnormal is far below 2^-150
+    const int sh = 926 - e;                    // >= 30
+    if (sh > 54) return __uint_as_float(sign);
+    const unsigned long long m53 = (1ull << 52) | ((unsigned long long)(hi & 0xfffffu) << 32) | lo;
+    const unsigned long long k = m53 >> sh, rem = m53 & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    const unsigned up = rem > half || (rem == half && (k & 1ull));
+    return __uint_as_float(sign | (unsigned)(k + up));
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned sign = u & 0x80000000u;
+    int e = (int)((u >> 23) & 0xffu);
+    unsigned m = u & 0x7fffffu;
+    if (e == 0xff) return __hiloint2double((int)(sign | 0x7ff00000u | (m ? 0x80000u : 0u)), 0);
+    if (e == 0) {
+        if (m == 0) return __hiloint2double((int)sign, 0);
+        const int sh = __clz(m) - 8;  // moves the leading one to bit 23
+        m = (m << sh) & 0x7fffffu;
+        e = 1 - sh;
+    }
+    return __hiloint2double((int)(sign | ((unsigned)(e + 896) << 20) | (m >> 3)), (int)(m << 29));
+}
+
+template <typename T>
+__device__ __forceinline__ double to_f64(T v);
+template <>
+__device__ __forceinline__ double to_f64<double>(double v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ double to_f64<float>(float v) {
+    return f32_to_f64(v);
+}
+
 // Rounded products and sums that the compiler may not fuse into an FMA: the
 // prolongation's e = w (a + b) and psi += e are written with these in every
 // kernel, so that all kernels round them alike.
@@ -303,6 +359,8 @@ int smooth_fused_level_blocks(int op, int N, int nmax);
 cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g, int N, int P, int nsw, double beta);
 size_t sor_smem_bytes(int N, int P);
 cudaError_t init_sor_kernel_attributes();
+// k_assemble_rhs sums kAsmRows rows per thread before its FP64 block sum.
+constexpr int kAsmRows = 4;
 int assemble_blocks(int N);
 int monitor_blocks(int N);
 
@@ -378,6 +436,10 @@ cudaError_t launch_rhs_stage_mixed(cudaStream_t s, const float *psi32, int Ps, c
 cudaError_t launch_thom_mixed(cudaStream_t s, const double *psi64, double *const w64[3], float *const w32[3], int N,
                               int P64, int P32, double U, int profile);
 cudaError_t launch_to32(cudaStream_t s, const double *src, int P64, float *dst, int P32, int N);
+// Compares f64_to_f32 / f32_to_f64 with the hardware conversions on n test
+// values; bad[0], bad[1] count the mismatches of each direction.
+cudaError_t launch_selftest_conversions(cudaStream_t s, long long n, unsigned long long seed,
+                                        unsigned long long *bad);
 
 // ---- batched engine (lc_batch.cu host side; kernels in lc_mg.cu and lc_mixed.cu)
 constexpr int kMaxBatch = 256;

@@ -356,9 +356,9 @@ __device__ __forceinline__ double up_body(int bx, int by, const T *__restrict__ 
             int c = y * LP + x;
             if (cor.psi64) {
                 size_t c64 = (size_t)gj * cor.P64 + gi;
-                double pnew = cor.psi64[c64] + (double)sp[c];
+                double pnew = cor.psi64[c64] + to_f64<T>(sp[c]);
                 cor.psi64[c64] = pnew;
-                if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + gi] = (float)pnew;
+                if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + gi] = f64_to_f32(pnew);
             } else {
                 psi_out[(size_t)gj * P + gi] = sp[c];
             }

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     float v = 0.0f;
     double rho;
     if (rho_halo<double, OP>(psi, g, N, P, i0, j, rho)) {
-        float r = (float)rho;
+        float r = f64_to_f32(rho);
         r32[(size_t)j * P32 + i0 - 1 + (int)(threadIdx.x & 31)] = r;
         v = r * r;
     }
@@ -83,9 +83,9 @@ __global__ void __launch_bounds__(kBX *kBY)
     int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     if (i >= N || j >= N) return;
     size_t c = (size_t)j * P64 + i;
-    double p = psi[c] + (double)e[(size_t)j * Pe + i];
+    double p = psi[c] + f32_to_f64(e[(size_t)j * Pe + i]);
     psi[c] = p;
-    if (psi32) psi32[(size_t)j * P32 + i] = (float)p;
+    if (psi32) psi32[(size_t)j * P32 + i] = f64_to_f32(p);
 }
 
 // L(omega) in FP32 from the FP32 shadows, stage combination in FP64 (see
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kBX *kBY)
         float ty = v * ((wN - wS) * inv2h);
         L = (L - tx) - ty;
     }
-    double Ld = (double)L, wPd = in64[c64];
+    double Ld = f32_to_f64(L), wPd = in64[c64];
     double o;
     if (k.mode == 3) {
         o = fma(k.bdt, Ld, fma(k.a1, wPd, acc[c64]));
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kBX *kBY)
         else if (k.mode == 2) acc[c64] = fma(k.acc_L, Ld, fma(k.acc_in, wPd, acc[c64]));
     }
     out64[c64] = o;
-    out32[c] = (float)o;
+    out32[c] = f64_to_f32(o);
 }
 
 struct Walls {
@@ -164,7 +164,7 @@ __global__ void k_thom_mixed(const double *__restrict__ psi, Walls w, int N, int
     }
     for (int b = 0; b < 3; ++b) {
         w.w64[b][(size_t)j * P64 + i] = val;
-        w.w32[b][(size_t)j * P32 + i] = (float)val;
+        w.w32[b][(size_t)j * P32 + i] = f64_to_f32(val);
     }
 }
 
@@ -173,7 +173,7 @@ __global__ void k_to32(const double *__restrict__ src, int P64, float *__restric
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y * blockDim.y + threadIdx.y;
     if (i > N || j > N) return;
-    dst[(size_t)j * P32 + i] = (float)src[(size_t)j * P64 + i];
+    dst[(size_t)j * P32 + i] = f64_to_f32(src[(size_t)j * P64 + i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kBX *kBY)
             float ty = v * ((wN - wS) * inv2h);
             L = (L - tx) - ty;
         }
-        Ld = (double)L;
+        Ld = f32_to_f64(L);
     }
     double bdt = k.bdt * cv.dt, o;
     if (k.mode == 3) {
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(kBX *kBY)
         else if (k.mode == 2) acc[c] = fma(k.acc_L * cv.dt, Ld, fma(k.acc_in, wPd, acc[c]));
     }
     out64[c] = o;
-    if (!RHS64) cv.Ws[stage_out(stage)][c] = (float)o;
+    if (!RHS64) cv.Ws[stage_out(stage)][c] = f64_to_f32(o);
 }
 
 // Poisson right-hand side (as k_assemble_rhs) of every cavity's new stage
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(kBX *kBY)
     float v = 0.0f;
     double rho;
     if (cv.active && rho_halo<double, OP>(cv.psi64, cv.g64, N, P, i0, j, rho)) {
-        float rf = (float)rho;
+        float rf = f64_to_f32(rho);
         cv.g32[0][(size_t)j * P + i0 - 1 + (int)(threadIdx.x & 31)] = rf;
         v = rf * rf;
     }
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(kBX *kBY) k_psi32_batch(const BatchCav *cav, c
     int i = 1 + bx * kBX + threadIdx.x, j = 1 + by * kBY + threadIdx.y;
     if (i >= N || j >= N) return;
     size_t c = (size_t)j * P + i;
-    cv.psi32[c] = (float)cv.psi64[c];
+    cv.psi32[c] = f64_to_f32(cv.psi64[c]);
 }
 
 // Thom's wall vorticity for every cavity (blockIdx.y = cavity), uniform lid U.
@@ -402,7 +402,7 @@ __global__ void k_thom_batch(const BatchCav *cav, double U) {
     }
     for (int b = 0; b < 3; ++b) {
         cv.W[b][(size_t)j * P + i] = val;
-        cv.Ws[b][(size_t)j * P + i] = (float)val;
+        cv.Ws[b][(size_t)j * P + i] = f64_to_f32(val);
     }
 }
 
@@ -488,6 +488,86 @@ cudaError_t launch_thom_mixed(cudaStream_t s, const double *psi64, double *const
     }
     int n = 4 * (N - 1) + 4;
     (void)launch_pdl(k_thom_mixed, (n + 255) / 256, 256, 0, s, psi64, w, N, P64, P32, U, profile);
+    return cudaGetLastError();
+}
+
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {  // SplitMix64 finaliser
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ bool same_bits_f(float a, float b) {
+    return __float_as_uint(a) == __float_as_uint(b) || (a != a && b != b);
+}
+
+__device__ __forceinline__ bool same_bits_d(double a, double b) {
+    return __double_as_longlong(a) == __double_as_longlong(b) || (a != a && b != b);
+}
+
+// Value k of the conversion test: fixed edge cases first, then four kinds
+// of generated FP64 patterns (raw 64-bit words; exponents around the FP32
+// range with random mantissas; the same with the 29 rounded-off bits at or
+// next to the halfway point; the FP32 subnormal range with ties at the
+// subnormal rounding position) and FP32 patterns (raw, subnormal).
+__device__ double conv_case(long long k, unsigned long long seed, float &f) {
+    const double edge[] = {0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.4028235677973366e38,
+                           3.4028235677973362e38, 3.4028235677973370e38, 6.805646932770577e38,
+                           1.1754943508222875e-38, 1.1754942106924411e-38, 5.877471754111438e-39,
+                           1.401298464324817e-45, 7.006492321624085e-46, 7.006492321624087e-46,
+                           2.1019476964872256e-45, 4.9406564584124654e-324, 2.2250738585072014e-308,
+                           1.7976931348623157e308, __longlong_as_double(0x7ff0000000000000ll),
+                           __longlong_as_double(0xfff0000000000000ll), __longlong_as_double(0x7ff8000000000001ll),
+                           0.1, 1.0 / 3.0, 1e-40, -1e-44};
+    const int nedge = (int)(sizeof(edge) / sizeof(edge[0]));
+    const unsigned long long u = mix64(seed ^ mix64((unsigned long long)k));
+    f = __uint_as_float((unsigned)(u >> 7));
+    if (k < nedge) {
+        f = (float)edge[k];
+        return edge[k];
+    }
+    const unsigned long long sign = u & 0x8000000000000000ull, mant = u & 0xfffffffffffffull;
+    switch (k & 3) {
+        case 0:
+            if (k & 4) f = __uint_as_float((unsigned)(u >> 32) & 0x807fffffu);  // FP32 subnormals
+            return __longlong_as_double((long long)u);
+        case 1: {
+            const unsigned long long e = 853 + ((u >> 52) & 0x7ffull) % 320;
+            return __longlong_as_double((long long)(sign | (e << 52) | mant));
+        }
+        case 2: {
+            const unsigned long long e = 853 + ((u >> 52) & 0x7ffull) % 320;
+            const unsigned long long low[4] = {0x10000000ull, 0x0fffffffull, 0x10000001ull, 0ull};
+            return __longlong_as_double((long long)(sign | (e << 52) | (mant & ~0x1fffffffull) | low[(u >> 40) & 3]));
+        }
+        default: {
+            const unsigned long long e = 840 + ((u >> 52) & 0x7ffull) % 60;  // FP32 subnormal results
+            const int sh = 926 - (int)e;
+            unsigned long long m = mant;
+            if (((u >> 41) & 1) && sh >= 1 && sh <= 52) m = (m & ~((1ull << sh) - 1)) | (1ull << (sh - 1));  // a tie
+            m &= 0xfffffffffffffull;
+            return __longlong_as_double((long long)(sign | (e << 52) | m));
+        }
+    }
+}
+
+__global__ void k_selftest_conversions(long long n, unsigned long long seed, unsigned long long *bad) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        float f;
+        const double d = conv_case(k, seed, f);
+        if (!same_bits_f(f64_to_f32(d), __double2float_rn(d))) atomicAdd(bad, 1ull);
+        if (!same_bits_d(f32_to_f64(f), (double)f)) atomicAdd(bad + 1, 1ull);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_selftest_conversions(cudaStream_t s, long long n, unsigned long long seed,
+                                        unsigned long long *bad) {
+    k_selftest_conversions<<<1216, 256, 0, s>>>(n, seed, bad);
     return cudaGetLastError();
 }
 

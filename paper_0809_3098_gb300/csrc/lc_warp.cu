@@ -317,14 +317,14 @@ __device__ __forceinline__ void wup(const WTile &t, const float *__restrict__ e_
         int gj = t.gy0 + y;
         double *row = cor.psi64 + (size_t)gj * cor.P64;
         if (o0) {
-            double p = row[i0] + (double)e0[y];
+            double p = row[i0] + f32_to_f64(e0[y]);
             row[i0] = p;
-            if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + i0] = (float)p;
+            if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + i0] = f64_to_f32(p);
         }
         if (o1) {
-            double p = row[i0 + 1] + (double)e1[y];
+            double p = row[i0 + 1] + f32_to_f64(e1[y]);
             row[i0 + 1] = p;
-            if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + i0 + 1] = (float)p;
+            if (cor.psi32) cor.psi32[(size_t)gj * cor.P32 + i0 + 1] = f64_to_f32(p);
         }
     }
 }

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
         "lc_get_params": ([vp, _dp], ci),
         "lc_launch_stats": ([vp, _dp], ci),
         "lc_bench_kernel": ([vp, ci, ci, _dp], ci),
+        "lc_selftest_conversions": ([ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)], ci),
         "lc_monitor_noalloc": ([ci, vp, vp, vp, vp, sz, cd, vp, vp], ci),
         "lc_batch_create": ([ci, ctypes.POINTER(ci), _dp, _dp, cd, ci], vp),
         "lc_batch_destroy": ([vp], None),
@@ -201,6 +202,14 @@ def lc_bench_kernel(ctx: int, kernel: int, reps: int) -> np.ndarray:
     out = np.zeros(4)
     _check(lib().lc_bench_kernel(ctx, kernel, reps, _p(out)), "lc_bench_kernel")
     return out
+
+
+def lc_selftest_conversions(n: int, seed: int = 0) -> tuple[int, int]:
+    """Mismatches (FP64 -> FP32, FP32 -> FP64) of the library's integer
+    conversions against the hardware's on n generated values."""
+    out = (ctypes.c_longlong * 2)()
+    _check(lib().lc_selftest_conversions(n, seed, out), "lc_selftest_conversions")
+    return out[0], out[1]
 
 
 LC_NOALLOC_MAX_N = 8192
