@@ -359,8 +359,9 @@ int smooth_fused_level_blocks(int op, int N, int nmax);
 cudaError_t launch_sor_lex(cudaStream_t s, int op, double *psi, const double *g, int N, int P, int nsw, double beta);
 size_t sor_smem_bytes(int N, int P);
 cudaError_t init_sor_kernel_attributes();
-// k_assemble_rhs sums kAsmRows rows per thread before its FP64 block sum.
-constexpr int kAsmRows = 4;
+// k_assemble_rhs keeps one row per thread: its partial sums of g^2 then
+// follow the 32 x 8 tiles of the batched assembly, so single and batched
+// cavities compare their residuals with the same ||g||.
 int assemble_blocks(int N);
 int monitor_blocks(int N);
 

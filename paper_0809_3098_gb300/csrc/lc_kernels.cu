@@ -376,21 +376,17 @@ __global__ void __launch_bounds__(kBX *kBY)
     pdl_enter();
     __shared__ double sh[32];
     int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    int j0 = 1 + blockIdx.y * (blockDim.y * kAsmRows) + threadIdx.y;
+    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
     double v = 0.0;
-#pragma unroll
-    for (int k = 0; k < kAsmRows; ++k) {  // kAsmRows rows per thread: one FP64 block sum per kAsmRows rows
-        int j = j0 + k * (int)blockDim.y;
-        if (i < N && j < N) {
-            size_t c = (size_t)j * P + i;
-            double val;
-            if (OP == 1)
-                val = h2 * fma(8.0, w[c], (w[c + 1] + w[c - 1]) + (w[c + P] + w[c - P])) * (1.0 / 40.0);
-            else
-                val = 0.25 * h2 * w[c];
-            g[c] = val;
-            v = fma(val, val, v);
-        }
+    if (i < N && j < N) {
+        size_t c = (size_t)j * P + i;
+        double val;
+        if (OP == 1)
+            val = h2 * fma(8.0, w[c], (w[c + 1] + w[c - 1]) + (w[c + P] + w[c - P])) * (1.0 / 40.0);
+        else
+            val = 0.25 * h2 * w[c];
+        g[c] = val;
+        v = val * val;
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) gpart[blockIdx.y * gridDim.x + blockIdx.x] = v;
@@ -589,7 +585,7 @@ int residual_norm_blocks(int N) { return residual_blocks_x(N) * ((N - 1 + kRY - 
 int residual_norm64_blocks(int N) {
     return residual_blocks_x(N) * ((N - 1 + kRY * kNormRows - 1) / (kRY * kNormRows));
 }
-int assemble_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY * kAsmRows - 1) / (kBY * kAsmRows)); }
+int assemble_blocks(int N) { return ((N - 1 + kBX - 1) / kBX) * ((N - 1 + kBY - 1) / kBY); }
 int monitor_blocks(int N) { return ((N + 1 + kBX - 1) / kBX) * ((N + 1 + kBY - 1) / kBY); }
 
 template <typename T>
@@ -606,7 +602,7 @@ cudaError_t launch_residual_norm(cudaStream_t s, int op, const T *psi, const T *
 cudaError_t launch_assemble_rhs(cudaStream_t s, int op, const double *omega, double *g, int N, int P,
                                 double *gpart) {
     double h = 1.0 / N;
-    dim3 grid = grid2(N - 1, N - 1, kBX, kBY * kAsmRows), blk(kBX, kBY);
+    dim3 grid = grid2(N - 1, N - 1, kBX, kBY), blk(kBX, kBY);
     if (op == 1)
         (void)launch_pdl(k_assemble_rhs<1>, grid, blk, 0, s, omega, g, N, P, h * h, gpart);
     else
