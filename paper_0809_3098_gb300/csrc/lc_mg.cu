@@ -11,7 +11,10 @@
 //            correction, nu2 colour sweeps, write the tile's own psi and (on
 //            the fine level) the tile's sum of squared residuals;
 //  k_coarse: a whole V-cycle of the coarsest levels in one block, every level
-//            held in shared memory.
+//            held in shared memory;
+//  k_coarse_cluster: the same V-cycle from a larger level down, its larger
+//            levels split by rows over the blocks of a thread-block cluster
+//            (distributed shared memory, a cluster barrier per phase).
 //
 // A tile owns an aligned block of TX x TY interior nodes and recomputes a halo
 // around it.  Invalid values enter a tile from its edge and spread one
