@@ -77,14 +77,29 @@ __device__ __forceinline__ T gs_value(const T *__restrict__ psi, const T *__rest
 // row, so the diagonal sum d4 = V(i+1) + V(i-1), with the column sums
 // V(k) = psi(k, j+1) + psi(k, j-1), takes V(i-1) from the lane to the left
 // (the same additions in the same order as gs_value, one fewer per node).
+// Lane 0 of each warp only supplies that column sum to lane 1 and updates no
+// node: computing its own left sum would be a warp-wide FP64 instruction for
+// one lane, as dear on GB300 (~64 clocks) as one for all 32.
 //
 // colour_item does the work of thread (a, b) of a phase (a: the colour
-// node's column index, b: its row pair); the 32 lanes of a warp must hold 32
-// consecutive a of one b.  L2 = true reads psi through L2 (for the fused
+// node's column index, b: its row pair); the lanes of a warp must hold
+// consecutive a of one b, for the compact operator a = 31 w + lane - 1 (lane
+// 0 the halo, see colour_a).  L2 = true reads psi through L2 (for the fused
 // kernel, whose blocks read values other blocks wrote in the same launch).
 template <bool L2, typename T>
 __device__ __forceinline__ T ldp(const T *p) {
     return L2 ? __ldcg(p) : *p;
+}
+
+// Colour column index of lane `lane` of warp-sized item w of a row: 31 nodes
+// per warp for the compact operator (lane 0 a halo), 32 for the 5-point one.
+template <int OP>
+__device__ __forceinline__ int colour_a(int w, int lane) {
+    return OP == 1 ? 31 * w + lane - 1 : 32 * w + lane;
+}
+template <int OP>
+__host__ __device__ constexpr int colour_per_warp() {
+    return OP == 1 ? 31 : 32;
 }
 
 template <typename T, int OP, bool RELAX, bool L2>
@@ -102,7 +117,7 @@ __device__ __forceinline__ void colour_item(T *psi, const T *__restrict__ g, int
     if (OP == 1) {
         // every lane of the warp reaches the shuffles; lanes past the grid
         // load nothing and store nothing
-        bool rowok = j < N, ok = rowok && i < N;
+        bool rowok = j < N, ok = rowok && i < N && (threadIdx.x & 31) != 0;
         bool second = ok && j + 2 < N;
         size_t c = (size_t)j * P + i, c2 = c + 2 * (size_t)P;
         bool colr = rowok && i + 1 <= N;  // column i + 1 exists (it may be the wall)
@@ -112,11 +127,6 @@ __device__ __forceinline__ void colour_item(T *psi, const T *__restrict__ g, int
         T V2r = (colr && j + 2 < N) ? ldp<L2>(psi + c2 + P + 1) + m_e : T(0);
         T Vl = __shfl_up_sync(0xffffffffu, Vr, 1), V2l = __shfl_up_sync(0xffffffffu, V2r, 1);
         if (!ok) return;
-        if ((threadIdx.x & 31) == 0) {
-            T m_w = ldp<L2>(psi + c + P - 1);
-            Vl = m_w + ldp<L2>(psi + c - P - 1);
-            if (second) V2l = ldp<L2>(psi + c2 + P - 1) + m_w;
-        }
         T n4 = (ldp<L2>(psi + c + 1) + ldp<L2>(psi + c - 1)) + (m_c + ldp<L2>(psi + c - P));
         T v1 = fma(T(0.2), n4, fma(T(0.05), Vr + Vl, g[c])), v2 = T(0);
         if (second) {
@@ -160,7 +170,8 @@ template <typename T, int OP, bool RELAX>
 __global__ void __launch_bounds__(kBX *kBY)
     k_smooth_colour(T *__restrict__ psi, const T *__restrict__ g, int N, int P, int colour, T beta) {
     pdl_enter();
-    colour_item<T, OP, RELAX, false>(psi, g, N, P, colour, beta, blockIdx.x * blockDim.x + threadIdx.x,
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;  // blockDim.x = 32: one warp per block row
+    colour_item<T, OP, RELAX, false>(psi, g, N, P, colour, beta, colour_a<OP>(t >> 5, t & 31),
                                      blockIdx.y * blockDim.y + threadIdx.y);
 }
 
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(256)
     k_smooth_fused(T *psi, const T *__restrict__ g, int N, int P, int nsweeps, T beta, DevState *ds, int extra) {
     const int na = N / 2;                              // colour nodes per row: at most N / 2
     const int nb = OP == 1 ? (N / 2 + 1) / 2 : N / 2;  // row pairs
-    const int nchunk = (na + 31) / 32, items = nchunk * nb;
+    const int nchunk = (na + colour_per_warp<OP>() - 1) / colour_per_warp<OP>(), items = nchunk * nb;
     const int lo = (int)((long long)items * blockIdx.x / gridDim.x);
     const int hi = (int)((long long)items * (blockIdx.x + 1) / gridDim.x);
     const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5, lane = threadIdx.x & 31;
@@ -218,7 +229,7 @@ __global__ void __launch_bounds__(256)
         for (int col = 0; col < ncol; ++col) {
             if (s > 0 || col > 0) grid_barrier(ds, gridDim.x + extra);
             for (int w = lo + wib; w < hi; w += nwb) {
-                int b = w / nchunk, a = (w - b * nchunk) * 32 + lane;
+                int b = w / nchunk, a = colour_a<OP>(w - b * nchunk, lane);
                 colour_item<T, OP, RELAX, true>(psi, g, N, P, col, beta, a, b);
             }
         }
@@ -538,8 +549,8 @@ cudaError_t launch_smooth_colour(cudaStream_t s, int op, T *psi, const T *g, int
     dim3 blk(kBX, kSmY);
     bool relax = beta != T(1);
     if (op == 1) {
-        int n = N / 2;                      // at most this many nodes of one parity per direction
-        dim3 grid = grid2(n, (n + 1) / 2, kBX, kSmY);  // two rows per thread
+        int n = N / 2;  // at most this many nodes of one parity per direction
+        dim3 grid((n + colour_per_warp<1>() - 1) / colour_per_warp<1>(), ((n + 1) / 2 + kSmY - 1) / kSmY);
         if (relax)
             (void)launch_pdl(k_smooth_colour<T, 1, true>, grid, blk, 0, s, psi, g, N, P, colour, beta);
         else
@@ -826,7 +837,8 @@ template cudaError_t launch_smooth_fused<double>(cudaStream_t, int, double *, co
 
 int smooth_fused_level_blocks(int op, int N, int nmax) {
     const int na = N / 2, nb = op == 1 ? (N / 2 + 1) / 2 : N / 2;
-    const int items = ((na + 31) / 32) * nb;  // warp-sized items of k_smooth_fused
+    const int per = op == 1 ? colour_per_warp<1>() : colour_per_warp<0>();
+    const int items = ((na + per - 1) / per) * nb;  // warp-sized items of k_smooth_fused
     const int want = (items + 7) / 8;         // one item per warp of a 256-thread block
     return want < 1 ? 1 : (want < nmax ? want : nmax);
 }
