@@ -302,14 +302,10 @@ __global__ void __launch_bounds__(kRT *kRT)
     psic[cc] = T(0);
 }
 
-// Bilinear prolongation of the coarse correction, added to the fine field.
+// Bilinear prolongation of the coarse correction onto fine node (i, j), added to psi.
 template <typename T>
-__global__ void __launch_bounds__(kBX *kBY)
-    k_prolong_correct(T *__restrict__ psi, int Nf, int Pf, const T *__restrict__ ec, int Pc) {
-    pdl_enter();
-    int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= Nf || j >= Nf) return;
+__device__ __forceinline__ void prolong_node(T *__restrict__ psi, int Pf, const T *__restrict__ ec, int Pc, int i,
+                                             int j) {
     int I = i >> 1, J = j >> 1;
     size_t cc = (size_t)J * Pc + I;
     T e;
@@ -323,6 +319,24 @@ __global__ void __launch_bounds__(kBX *kBY)
         e = mul_rn(T(0.25), (ec[cc] + ec[cc + 1]) + (ec[cc + Pc] + ec[cc + Pc + 1]));
     size_t c = (size_t)j * Pf + i;
     psi[c] = add_rn(psi[c], e);
+}
+
+// Bilinear prolongation of the coarse correction, added to the fine field.
+// A block covers 64 columns x 8 rows; the lanes of a warp take every other
+// column of one row in each of two passes, so a warp's nodes share one
+// (i, j) parity and take one branch: the four parity classes need 0-3 FP64
+// operations, and on GB300 a divergent branch costs its full warp-wide FP64
+// issue (~64 clocks) per instruction whatever its lane count.
+template <typename T>
+__global__ void __launch_bounds__(kBX *kBY)
+    k_prolong_correct(T *__restrict__ psi, int Nf, int Pf, const T *__restrict__ ec, int Pc) {
+    pdl_enter();
+    const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+    if (j >= Nf) return;
+    for (int p = 0; p < 2; ++p) {
+        const int i = 1 + p + blockIdx.x * (2 * blockDim.x) + 2 * threadIdx.x;
+        if (i < Nf) prolong_node<T>(psi, Pf, ec, Pc, i, j);
+    }
 }
 
 // Coarsest grid (2, 3, 5 or 7 intervals: at most 36 unknowns, one thread each
@@ -579,7 +593,8 @@ cudaError_t launch_residual_restrict(cudaStream_t s, int op, const T *psi, const
 
 template <typename T>
 cudaError_t launch_prolong_correct(cudaStream_t s, T *psi, int Nf, int Pf, const T *ec, int Pc) {
-    (void)launch_pdl(k_prolong_correct<T>, grid2(Nf - 1, Nf - 1, kBX, kBY), dim3(kBX, kBY), 0, s, psi, Nf, Pf, ec, Pc);
+    (void)launch_pdl(k_prolong_correct<T>, grid2(Nf - 1, Nf - 1, 2 * kBX, kBY), dim3(kBX, kBY), 0, s, psi, Nf, Pf,
+                     ec, Pc);
     return cudaGetLastError();
 }
 

@@ -545,9 +545,16 @@ __device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int 
         const T *ec = sg + LP * LP;
         const unsigned m = n - 1;
         if constexpr (kPacked<T>) {
-            for (unsigned q = tid; q < m * m; q += nt) {
-                const unsigned jj = q / m;
-                prolong_add<T>(sp, ec, LP, LPc, 1 + (int)(q - jj * m), 1 + (int)jj);
+            // one (i, j) parity class after the other, so that a warp's nodes
+            // take one branch of prolong_add (0-3 FP64 operations)
+            for (int cls = 0; cls < 4; ++cls) {
+                const int i0 = 1 + (cls & 1), j0 = 1 + (cls >> 1);
+                const unsigned nx = m >= (unsigned)i0 ? (m - i0) / 2 + 1 : 0;
+                const unsigned ny = m >= (unsigned)j0 ? (m - j0) / 2 + 1 : 0;
+                for (unsigned q = tid; q < nx * ny; q += nt) {
+                    const unsigned yy = q / nx;
+                    prolong_add<T>(sp, ec, LP, LPc, i0 + 2 * (int)(q - yy * nx), j0 + 2 * (int)yy);
+                }
             }
         } else {
             for (int j = 1 + ty; j < n; j += by)
@@ -868,19 +875,22 @@ __global__ void __launch_bounds__(512)
             for (int j = ylo + ty; j <= yhi; j += by) {
                 const T *c0 = crow(j >> 1), *c1 = crow((j >> 1) + 1);
                 T *row = ps + (j - st.lo + 1) * LP;
-                for (int i = 1 + tx; i <= m; i += bx) {
-                    const int I = i >> 1;
-                    T e;
-                    if (!(i & 1) && !(j & 1))
-                        e = c0[I];
-                    else if ((i & 1) && !(j & 1))
-                        e = mul_rn(T(0.5), c0[I] + c0[I + 1]);
-                    else if (!(i & 1) && (j & 1))
-                        e = mul_rn(T(0.5), c0[I] + c1[I]);
-                    else
-                        e = mul_rn(T(0.25), (c0[I] + c0[I + 1]) + (c1[I] + c1[I + 1]));
-                    row[i] = add_rn(row[i], e);
-                }
+                // odd columns, then even ones: the lanes of a warp share one
+                // (i, j) parity and so one branch
+                for (int p = 1; p <= 2; ++p)
+                    for (int i = p + 2 * tx; i <= m; i += 2 * bx) {
+                        const int I = i >> 1;
+                        T e;
+                        if (!(i & 1) && !(j & 1))
+                            e = c0[I];
+                        else if ((i & 1) && !(j & 1))
+                            e = mul_rn(T(0.5), c0[I] + c0[I + 1]);
+                        else if (!(i & 1) && (j & 1))
+                            e = mul_rn(T(0.5), c0[I] + c1[I]);
+                        else
+                            e = mul_rn(T(0.25), (c0[I] + c0[I + 1]) + (c1[I] + c1[I + 1]));
+                        row[i] = add_rn(row[i], e);
+                    }
             }
         }
         cl.sync();
