@@ -235,7 +235,7 @@ KERNELS = {
 # DRAM bytes (read + write) of one launch of the roofline kernel, from one ncu
 # capture of the benchmark's own command (profiles/smoother_fp64_1024_traffic.md);
 # a kernel or grid size without an entry reports traffic null.
-MEASURED_TRAFFIC = {("k_smooth_colour<double,compact> (fine level, one colour phase)", 1024): 12728320 + 0}
+MEASURED_TRAFFIC = {("k_smooth_colour<double,compact> (fine level, one colour phase)", 1024): 12728576 + 0}
 
 
 def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> dict:
