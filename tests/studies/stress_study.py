@@ -37,7 +37,7 @@ def main():
     ap.add_argument("--Re", type=float, default=30000.0)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--every", type=int, default=5000)
-    ap.add_argument("--out", default="gpurun_out/stress")
+    ap.add_argument("--out", default="stress_out")
     args = ap.parse_args()
     import torch
 
