@@ -27,6 +27,8 @@
 
 #include <cooperative_groups.h>
 
+#include <atomic>
+
 namespace lcx {
 
 namespace {
@@ -1098,12 +1100,12 @@ cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg,
     return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 0>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
 }
 
-// Largest cluster (16, else 8, else 0) that the device can schedule for the
-// coarse cluster kernel with its minimum shared memory.
-int coarse_cluster_size() {
-    static int cached = -1;
-    if (cached >= 0) return cached;
-    int best = 0;
+// Largest cluster (16, else 8, else 0) that the current device can schedule
+// for the coarse cluster kernel with its largest shared memory; found by
+// init_mg_kernel_attributes (after the non-portable size is allowed).
+static std::atomic<int> g_cluster_size{0};
+
+static int query_cluster_size() {
     for (int C : {16, 8}) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(C);
@@ -1117,15 +1119,14 @@ int coarse_cluster_size() {
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, (const void *)k_coarse_cluster<double, 1>, &cfg) == cudaSuccess && n > 0) {
-            best = C;
-            break;
-        }
+        const void *k = (const void *)k_coarse_cluster<double, 1>;
+        if (cudaOccupancyMaxActiveClusters(&n, k, &cfg) == cudaSuccess && n > 0) return C;
         cudaGetLastError();  // a size the device cannot schedule is not an error here
     }
-    cached = best;
-    return best;
+    return 0;
 }
+
+int coarse_cluster_size() { return g_cluster_size.load(); }
 
 namespace {
 
@@ -1241,6 +1242,7 @@ cudaError_t init_mg_kernel_attributes() {
     cudaError_t e = set_attrs_t<double>();
     if (e == cudaSuccess) e = set_cluster_attrs_t<double>();
     if (e == cudaSuccess) e = set_cluster_attrs_t<float>();
+    if (e == cudaSuccess) g_cluster_size.store(query_cluster_size());
     if (e == cudaSuccess) e = set_attrs_t<float>();
     if (e == cudaSuccess) e = set_batch_attrs_t<0>();
     if (e == cudaSuccess) e = set_batch_attrs_t<1>();
