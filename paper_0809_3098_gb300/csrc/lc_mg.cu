@@ -709,6 +709,7 @@ __global__ void __launch_bounds__(1024) k_coarse_batch(BatchCav *cav, int nu1, i
 // Restriction and prolongation read the rows they need from whichever block
 // owns them.  Every value is computed by the expression the one-block kernel
 // uses for it, so both kernels give the same bits.
+
 // Shared-memory layout of k_coarse_cluster (element offsets, the same in
 // every block): the strips of the nd distributed levels (psi with its two
 // halo rows, g, residual), then the one-block levels in smem_vcycle's layout
