@@ -92,3 +92,26 @@ def test_workspace_bytes(L):
     a, b = lc.lc_workspace_bytes(512, 0), lc.lc_workspace_bytes(1024, 0)
     assert 3.5 < b / a < 4.5
     assert b % 256 == 0
+
+
+def test_batch_options_validate_without_gpu(L):
+    """Batch creation and option checks are host-side: no device is touched."""
+    import ctypes
+
+    N = (ctypes.c_int * 2)(128, 256)
+    Re = (ctypes.c_double * 2)(1000.0, 5000.0)
+    b = L.lc_batch_create(2, N, Re, None, 1e-10, lc.LC_PREC_MIXED)
+    assert b
+    try:
+        for key, ok, bad in (("pdl", (0, 1), (2, -1)), ("graph", (0, 1), (2,)), ("nu1", (1, 4), (0, 5)),
+                             ("rhs64", (0, 1), (3,))):
+            for v in ok:
+                assert L.lc_batch_set_option(b, key.encode(), float(v)) == lc.LC_OK, (key, v)
+            for v in bad:
+                assert L.lc_batch_set_option(b, key.encode(), float(v)) == lc.LC_ERR_ARG, (key, v)
+        assert L.lc_batch_set_option(b, b"nonsense", 1.0) == lc.LC_ERR_ARG
+    finally:
+        L.lc_batch_destroy(b)
+    bad_N = (ctypes.c_int * 1)(100)
+    assert not L.lc_batch_create(1, bad_N, Re, None, 1e-10, lc.LC_PREC_MIXED)
+    assert not L.lc_batch_create(2, N, Re, None, 1e-10, lc.LC_PREC_FP64)
