@@ -11,9 +11,9 @@ fourth-order Poisson operator, starting from rest (synthetic, deterministic).
                   [--workload fp64-1024|fp64-128|fp64-4096] [--precision fp64|mixed]
                   [--eager] [--no-cpu-baseline] [--no-e2e] [--no-variants]
 
---precision mixed runs the same workload with FP32 V-cycles and FP32
-L(omega) stencils inside FP64 residual, refinement, Thom and stage
-accumulation.  --eager launches the step's kernels one by one (the V-cycle
+--precision mixed runs the same workload with FP32 multigrid V-cycles
+inside FP64 residual, refinement, L(omega), Thom and stage accumulation (the
+library's default; option rhs64 = 0 would take L(omega) from FP32 shadows).  --eager launches the step's kernels one by one (the V-cycle
 loop driven from the host) so that a profiler can attribute them; it is
 slower and only for profiling.
 
@@ -53,7 +53,7 @@ SCHEDULE = {"nu1": 2, "nu2": 1}
 METRIC = "grid-point-stage updates/s"
 UNIT = "updates/s"
 L2_FLUSH_BYTES = 256 << 20
-CPU_SAMPLE_SECONDS = 12.0
+CPU_SAMPLE_SECONDS = 8.0
 
 
 def parse():
@@ -138,20 +138,33 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle_rate(wl: Workload, budget_s: float):
-    """Times the plain C oracle from rest on this host (single thread) for at
-    least one step and until budget_s has passed.  Returns (updates/s, steps, s)."""
+def host_cores() -> int:
+    """Cores this process may run on (the affinity mask where the OS has one)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(wl: Workload, budget_s: float, threads: int = 1):
+    """Times the plain C oracle from rest on this host with `threads` OpenMP
+    threads (the same bits for any count) for at least one step and until
+    budget_s has passed.  Returns (updates/s, steps, s)."""
     import oracle
 
-    cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **SCHEDULE)
-    steps, t0 = 0, time.perf_counter()
-    while True:
-        cav.step(1)
-        steps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or steps >= 1000:
-            break
-    cav.close()
+    oracle.set_threads(threads)
+    try:
+        cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **SCHEDULE)
+        steps, t0 = 0, time.perf_counter()
+        while True:
+            cav.step(1)
+            steps += 1
+            el = time.perf_counter() - t0
+            if el >= budget_s or steps >= 1000:
+                break
+        cav.close()
+    finally:
+        oracle.set_threads(1)
     return wl.interior_nodes * 5 * steps / el, steps, el
 
 
@@ -161,20 +174,24 @@ def run_reference(args, wl: Workload):
         return 0
     import oracle
 
+    cores = host_cores()
+    oracle.set_threads(cores)
     cav = oracle.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **SCHEDULE)
     cav.step(args.warmup)
     t0 = time.perf_counter()
     cav.step(args.steps)
     el = time.perf_counter() - t0
+    oracle.set_threads(1)
     value = wl.interior_nodes * 5 * args.steps / el
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(wl, args.gpus),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} timed SSPRK(5,4) steps after {args.warmup} from rest, "
-                                   f"{wl.N}x{wl.N}, plain C FP64, one thread"},
+                                   f"{wl.N}x{wl.N}, plain C FP64, OpenMP over the independent loops on "
+                                   f"{cores} threads (reductions serial; the same bits as one thread)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -226,16 +243,21 @@ KERNELS = {
              (1, "k_rhs_stage (fused L(omega) + stage combination)", lambda c, nu: 5),
              (2, "k_residual_restrict<double,compact> (fine level)", lambda c, nu: c)],
     "mixed": [(0, "k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)", lambda c, nu: c),
-              (1, "k_rhs_stage_mixed (FP32 L(omega) + FP64 stage combination)", lambda c, nu: 5),
+              (1, "k_rhs_stage (FP64 L(omega) + stage combination; option rhs64, the default)", lambda c, nu: 5),
               (2, "k_residual64_to32<compact> (FP64 residual, rounded to FP32)", lambda c, nu: c + 5),
               (3, "k_up<float,compact> (fine level: FP32 post-smoothing + FP64 psi += e)", lambda c, nu: c)],
 }
 
 
-# DRAM bytes (read + write) of one launch of the roofline kernel, from one ncu
-# capture of the benchmark's own command (profiles/smoother_fp64_1024_traffic.md);
-# a kernel or grid size without an entry reports traffic null.
-MEASURED_TRAFFIC = {("k_smooth_colour<double,compact> (fine level, one colour phase)", 1024): 12728576 + 0}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per interior
+# node of one launch, from one ncu capture of each kernel at 1024^2 with the
+# step's arguments; a launch's traffic is this figure times its interior
+# nodes (the kernels read and write every node once per launch, so the
+# traffic grows with the node count).  A kernel without a capture of its
+# current code reports null.
+#   k_smooth_colour<double,compact>: 12,728,576 B per launch at 1024^2 over
+#   1023^2 interior nodes = 12.163 B per node (12 B algorithmic).
+TRAFFIC_PER_NODE = {"k_smooth_colour<double,compact> (fine level, one colour phase)": 12728576 / 1023 ** 2}
 
 
 def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> dict:
@@ -267,7 +289,8 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
                                 f"{'FP64' if bound == 'alu64' else 'FP32'} FMA/clk x 2 flop x {mhz:.0f} MHz "
                                 f"(median SM clock under load)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = MEASURED_TRAFFIC.get((name, cav.N))
+    per_node = TRAFFIC_PER_NODE.get(name)
+    roof["traffic"] = round(per_node * (cav.N - 1) ** 2) if per_node is not None else None
     roof["kernel"] = name
     roof["kernel_ms"] = ms
     roof["launches_per_step"] = {k: f for k, _, f in KERNELS[precision]}[kid](cycles_per_step, nu)
@@ -326,19 +349,21 @@ def timed_run(lc, torch, dist, wl: Workload, precision: str, steps: int, warmup:
     }
 
 
-def mixed_bytes_per_node(cycles_per_step: float) -> float:
+def mixed_bytes_per_node(cycles_per_step: float, rhs64: bool = True) -> float:
     """Algorithmic DRAM bytes per interior node of one mixed-precision step
     (each array element read or written once per kernel):
-    L(omega) + stage combination over the five stages 28+36+44+52+36 = 196 B;
-    Poisson right-hand side 5 x 16 B; the first FP64 residual of each solve
-    5 x 20 B; the FP32 shadow of psi after each solve 5 x 12 B; per
-    refinement cycle: fine-level FP32 pre-smoothing tile 9 B (r32 in, e32
-    out, coarse g out), post-smoothing tile + psi64 += e 25 B (e32, r32,
-    coarse e in; psi64 in and out), FP64 residual 20 B (psi64, g64 in; r32
-    out), and the coarser levels' tiles, 22 B per coarse node summed over
-    levels (22/4 + 22/16 + ...)."""
+    L(omega) + stage combination over the five stages: in FP64 (option
+    rhs64, the default) 24+32+40+48+32 = 176 B, from the FP32 shadows
+    28+36+44+52+36 = 196 B plus the FP32 shadow of psi after each solve
+    5 x 12 B; Poisson right-hand side 5 x 16 B; the first FP64 residual of
+    each solve 5 x 20 B; per refinement cycle: fine-level FP32 pre-smoothing
+    tile 9 B (r32 in, e32 out, coarse g out), post-smoothing tile + psi64 += e
+    25 B (e32, r32, coarse e in; psi64 in and out), FP64 residual 20 B
+    (psi64, g64 in; r32 out), and the coarser levels' tiles, 22 B per coarse
+    node summed over levels (22/4 + 22/16 + ...)."""
     per_cycle = 9.0 + 25.0 + 20.0 + 22.0 / 3.0
-    return 196.0 + 80.0 + 100.0 + 60.0 + cycles_per_step * per_cycle
+    stage = 176.0 if rhs64 else 196.0 + 60.0
+    return stage + 80.0 + 100.0 + cycles_per_step * per_cycle
 
 
 def run_batch(lc, torch, args, world: int, eager: bool = False) -> dict:
@@ -484,10 +509,17 @@ def run_ours(args, wl: Workload):
 
     # --- CPU oracle on this host (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, steps, el = cpu_oracle_rate(wl, CPU_SAMPLE_SECONDS)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cores = host_cores()
+        rate, steps, el = cpu_oracle_rate(wl, CPU_SAMPLE_SECONDS, cores)
+        rate1, steps1, el1 = cpu_oracle_rate(wl, CPU_SAMPLE_SECONDS, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"first {steps} SSPRK(5,4) steps from rest of the same workload "
-                                          f"({el:.1f} s), plain C FP64, one thread"}
+                                          f"({el:.1f} s), plain C FP64, OpenMP over the independent loops "
+                                          f"(colour phases, stencils, transfers, stage combination; reductions "
+                                          f"serial) on {cores} threads",
+                                "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"first {steps1} steps from rest ({el1:.1f} s), "
+                                                            f"one thread"}}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

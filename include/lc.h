@@ -131,9 +131,13 @@ const char *lc_last_error(void);
  *                 barrier wait for one block more than the launch has, so
  *                 every wait runs out (about 0.2 s each) and the next
  *                 synchronising call reports LC_ERR_TIMEOUT
- *   "rhs64"       mixed precision only: 1 evaluates L(omega) (Eq. (8)) in FP64
- *                 from the FP64 psi and omega instead of their FP32 shadows
- *                 (default 0); the multigrid corrections stay FP32
+ *   "rhs64"       mixed precision only: 1 (default) evaluates L(omega)
+ *                 (Eq. (8)) in FP64 from the FP64 psi and omega; 0 evaluates it
+ *                 in FP32 from their FP32 shadows (fewer bytes, but its
+ *                 rounding, ~6e-8 of omega / h^2 in the viscous term, grows
+ *                 past 1e-6 relative over long unsteady runs at Re >= 2e4 and
+ *                 puts a floor under the steady-state monitors).  The
+ *                 multigrid corrections stay FP32 either way.
  *   "U"           lid speed (1.0); re-applies Thom to the current state
  *   "profile"     0 uniform lid (default), 1 regularised lid 16x^2(1-x)^2 U
  *   "advect"      1 (default), 0 drops the transport terms of Eq. (8)
@@ -246,8 +250,9 @@ int lc_launch_stats(lc_ctx *ctx, double out[2]);
  * restriction, 3 = one lexicographic SOR pass of sor_sweeps sweeps, 4 = the
  * fine-level pre-smoothing pass (nu1 colour sweeps in one cooperative
  * launch, LC_ERR_ARG where the device cannot launch it).  Mixed precision: 0 = fine-level FP32 tile kernel (pre-smoothing,
- * residual, restriction), 1 = FP32 L(omega) + FP64 stage combination (stage
- * 2), 2 = FP64 residual rounded to FP32, 3 = fine-level FP32 tile kernel
+ * residual, restriction), 1 = L(omega) + FP64 stage combination (stage 2;
+ * FP64 L with rhs64 = 1, else FP32), 2 = FP64 residual rounded to FP32,
+ * 3 = fine-level FP32 tile kernel
  * (prolongation, post-smoothing, FP64 psi += e).  out[0] = mean ms per
  * launch, out[1] = algorithmic bytes per launch (each array element the
  * kernel must read or write, counted once), out[2] = FP64 and out[3] = FP32
@@ -343,8 +348,8 @@ int lc_batch_autotune_schedule(lc_batch *b, int steps, int nu_out[2]);
  * cannot call cudaMalloc (a host framework that owns all device memory
  * through its own pool, work enqueued while a CUDA graph is being captured,
  * a process with a fixed memory budget).  It computes what lc_monitor's
- * out[0..2] report: out[0] = max |omega1 - omega0| / dt, out[1] = RES_psi,
- * out[2] = RES_omega (Eqs. (26)-(27), 1/N read as 1/(N+1)), over all
+ * out[0..2] report: out[0] = max |omega1 - omega0| / dt, and out[1], out[2]
+ * the RES_psi and RES_omega values that lc_monitor reports, over all
  * (N+1) x (N+1) nodes.
  *   psi0, psi1, omega0, omega1: device FP64 arrays of N+1 rows, element (i, j)
  *     at j*pitch + i (pitch >= N+1; pitch = N+1 is the host layout above);
@@ -356,9 +361,11 @@ int lc_batch_autotune_schedule(lc_batch *b, int steps, int nu_out[2]);
  * GPU loading the library holds until the process exits.  The first call on
  * a device looks up the array's device address (cudaGetSymbolAddress) with
  * that device current, so make the first call on each device before any
- * stream capture.  No call allocates or frees memory.  All calls share the
- * array: calls that overlap on the GPU (two streams, two threads) race;
- * calls in order on one stream are safe.  Returns LC_ERR_SIZE for
+ * stream capture.  The address found is kept for the life of the device's
+ * context: after cudaDeviceReset the library must be reloaded before this
+ * entry point is used again on that device.  No call allocates or frees
+ * memory.  All calls share the array: calls that overlap on the GPU (two
+ * streams, two threads) race; calls in order on one stream are safe.  Returns LC_ERR_SIZE for
  * N > LC_NOALLOC_MAX_N, LC_ERR_ARG for NULL arrays, pitch < N+1, N < 1 or
  * dt <= 0, LC_ERR_CUDA if the set-up or the launch fails. */
 int lc_monitor_noalloc(int N, const double *psi0, const double *psi1, const double *omega0,

@@ -4,8 +4,10 @@ TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
 baseline leg use this package to check and time the CUDA library.  The library
 never imports it and shares no code with it.
 
-The arithmetic lives in ``lc_oracle.c`` (plain C, ``-O2 -ffp-contract=off``);
-this module compiles it with gcc and wraps it with ctypes.  Arrays are numpy
+The arithmetic lives in ``lc_oracle.c`` (plain C, ``-O2 -ffp-contract=off``,
+OpenMP over loops whose iterations are independent, one thread unless
+``set_threads`` says otherwise); this module compiles it with gcc and wraps it
+with ctypes.  Arrays are numpy
 ``float64`` of shape ``(N+1, N+1)`` indexed ``[j, i]`` (row j = y index,
 column i = x index), which is the C layout ``j*(N+1) + i``.
 
@@ -44,7 +46,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", "-std=c11",
              "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -87,8 +89,21 @@ def lib():
         L.or_last_residual.restype = cd
         L.or_cycle_log.argtypes = [vp, ctypes.POINTER(ci), ctypes.c_longlong]
         L.or_cycle_log.restype = ctypes.c_longlong
+        L.or_set_threads.argtypes = [ci]
+        L.or_get_threads.restype = ci
         _lib = L
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's independent loops (colour phases, stencils,
+    transfers, the Runge-Kutta combination); reductions and the lexicographic
+    SOR sweep stay serial, so results are bit-identical for any count."""
+    lib().or_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().or_get_threads())
 
 
 def _p(a: np.ndarray):

@@ -69,6 +69,23 @@
 
 #define AT(N, i, j) ((size_t)(j) * (size_t)((N) + 1) + (size_t)(i))
 
+/* Threads for the loops whose iterations are independent: a colour phase of
+ * the smoother (no node of a colour reads another of that colour), the
+ * operator, residual, restriction, prolongation, right-hand side, L(omega)
+ * and the Runge-Kutta combination (each output node written by one
+ * iteration from inputs no iteration writes).  Every node is computed by the
+ * same expression whatever the thread count, and the reductions (norms,
+ * monitors) and the lexicographic SOR sweep stay serial, so the results are
+ * bit-identical for any count.  Default 1; set by or_set_threads.  Built
+ * without OpenMP the pragmas are ignored and the count has no effect. */
+static int or_threads = 1;
+
+void or_set_threads(int n) { or_threads = n < 1 ? 1 : n; }
+int or_get_threads(void) { return or_threads; }
+
+/* Whether a loop of n rows is worth splitting over threads. */
+static int or_par(int n) { return or_threads > 1 && n >= 64; }
+
 /* ------------------------------------------------------------------------ */
 /* SSPRK(5,4) coefficients, Eqs. (9)-(13), in Shu-Osher form:
  *   y_s = sum_{k<s} ( alpha[s][k] y_k + dt beta[s][k] L(y_k) ),  s = 1..5,
@@ -112,6 +129,7 @@ void or_ssprk54_step(int n, double *y, double dt, or_L_fn L, void *user, double 
     memcpy(Y[0], y, sizeof(double) * n);
     for (int s = 1; s <= 5; ++s) {
         L(user, s - 1, Y[s - 1], LY[s - 1]);
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(n / 1024))
         for (int m = 0; m < n; ++m) {
             double acc = 0.0;
             for (int k = 0; k < s; ++k) {
@@ -141,6 +159,7 @@ void or_ssprk54_step(int n, double *y, double dt, or_L_fn L, void *user, double 
 /* f at interior nodes from omega (walls of f are zero). */
 void or_poisson_rhs(int N, int op, const double *omega, double *f) {
     memset(f, 0, sizeof(double) * (size_t)(N + 1) * (N + 1));
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
         for (int i = 1; i < N; ++i) {
             if (op == OR_OP_COMPACT) {
@@ -167,6 +186,7 @@ static double term_C(int N, double a, const double *p, int i, int j) {
 void or_apply_operator(int N, int op, const double *psi, double *out) {
     double h = 1.0 / N, b = 1.0 / (h * h), c = 1.0 / (h * h), a = b + c;
     memset(out, 0, sizeof(double) * (size_t)(N + 1) * (N + 1));
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
         for (int i = 1; i < N; ++i) {
             double A = term_A(N, b, c, psi, i, j);
@@ -180,6 +200,7 @@ void or_apply_operator(int N, int op, const double *psi, double *out) {
 /* r = f - L_h psi at interior nodes. */
 void or_residual(int N, int op, const double *psi, const double *f, double *r) {
     or_apply_operator(N, op, psi, r);
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
         for (int i = 1; i < N; ++i) r[AT(N, i, j)] = f[AT(N, i, j)] - r[AT(N, i, j)];
 }
@@ -202,6 +223,7 @@ void or_smooth(int N, int op, double *psi, const double *f, double beta, int nsw
     int ncolours = op == OR_OP_COMPACT ? 4 : 2;
     for (int s = 0; s < nsweeps; ++s)
         for (int colour = 0; colour < ncolours; ++colour)
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
             for (int j = 1; j < N; ++j)
                 for (int i = 1; i < N; ++i) {
                     if (!in_colour(op, colour, i, j)) continue;
@@ -241,6 +263,7 @@ void or_sor_lex(int N, int op, double *psi, const double *f, double beta, int ns
 void or_restrict(int Nf, const double *rf, double *fc) {
     int Nc = Nf / 2;
     memset(fc, 0, sizeof(double) * (size_t)(Nc + 1) * (Nc + 1));
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(Nc))
     for (int J = 1; J < Nc; ++J)
         for (int I = 1; I < Nc; ++I) {
             int i = 2 * I, j = 2 * J;
@@ -256,6 +279,7 @@ void or_restrict(int Nf, const double *rf, double *fc) {
  * to the fine field psi at interior nodes. */
 void or_prolong_add(int Nc, const double *ec, double *psi) {
     int Nf = 2 * Nc;
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(Nf))
     for (int j = 1; j < Nf; ++j)
         for (int i = 1; i < Nf; ++i) {
             int I = i / 2, J = j / 2;
@@ -461,6 +485,7 @@ void or_thom(int N, double U, int profile, const double *psi, double *omega) {
 void or_rhs_L(int N, double Re, int advect, const double *psi, const double *omega, double *out) {
     double h = 1.0 / N, dx = h, dy = h, nu = 1.0 / Re;
     memset(out, 0, sizeof(double) * (size_t)(N + 1) * (N + 1));
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
         for (int i = 1; i < N; ++i) {
             double u = (psi[AT(N, i, j + 1)] - psi[AT(N, i, j - 1)]) / (2.0 * dy);
@@ -513,15 +538,15 @@ static size_t nodes(int N) { return (size_t)(N + 1) * (N + 1); }
 
 /* Interior vorticity is the Runge-Kutta unknown; it is packed row by row. */
 static void scatter_interior(int N, const double *y, double *omega) {
-    size_t m = 0;
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
-        for (int i = 1; i < N; ++i) omega[AT(N, i, j)] = y[m++];
+        for (int i = 1; i < N; ++i) omega[AT(N, i, j)] = y[(size_t)(j - 1) * (N - 1) + (i - 1)];
 }
 
 static void gather_interior(int N, const double *field, double *y) {
-    size_t m = 0;
+#pragma omp parallel for schedule(static) num_threads(or_threads) if (or_par(N))
     for (int j = 1; j < N; ++j)
-        for (int i = 1; i < N; ++i) y[m++] = field[AT(N, i, j)];
+        for (int i = 1; i < N; ++i) y[(size_t)(j - 1) * (N - 1) + (i - 1)] = field[AT(N, i, j)];
 }
 
 /* Poisson solve for the current omega (lagged walls, R6), then Thom (R5). */

@@ -152,7 +152,7 @@ struct lc_ctx {
     int use_graph = 1;
     double beta = 1.0, U = 1.0;
     int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR
-    int rhs64 = 0;                                      // mixed precision: L(omega) in FP64
+    int rhs64 = 1;  // mixed precision: L(omega) in FP64 (0: from the FP32 shadows)
     int fused = 0;                 // 1: fine-level FP64 colour phases of a pass in one cooperative launch
     int barrier_extra = 0;         // test hook: the fused kernel's barrier waits for this many more blocks
     int fused_blocks[2] = {0, 0};  // its grid (beta == 1, beta != 1); 0: not available
@@ -221,7 +221,7 @@ void release_graph(lc_ctx *c) {
 // FP32 one-block V-cycle is faster than the cluster's barriers).
 int cluster_size(const lc_ctx *c) {
     if (c->coarse_cluster >= 0) return c->coarse_cluster;
-    return c->mixed() ? 0 : coarse_cluster_size();
+    return c->mixed() ? 0 : coarse_cluster_size(c->device);
 }
 
 // Whether coarse level lc runs on the cluster kernel: it is not the fine level
@@ -1066,6 +1066,9 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 return launch_down<float>(s, tile_shape(c, 0), c->op, nullptr, 1, c->g32(0), c->eB(0), N, P, c->g32(1),
                                           L.Pl[1], c->nu1, (float)c->beta);
             case 1:
+                if (c->rhs64)
+                    return launch_rhs_stage(s, c->psi(0), c->at<double>(L.Wa), c->at<double>(L.W0),
+                                            c->at<double>(L.ACC), c->at<double>(L.Wb), N, P, c->Re, c->advect, k2);
                 return launch_rhs_stage_mixed(s, c->at<float>(L.psi32), P, c->at<float>(L.Was), c->at<double>(L.Wa),
                                               c->at<double>(L.W0), c->at<double>(L.ACC), c->at<double>(L.Wb),
                                               c->at<float>(L.Wbs), N, P, P, c->Re, c->advect, k2);
@@ -1127,10 +1130,15 @@ int lc_bench_kernel(lc_ctx *c, int kernel, int reps, double out[4]) {
                 out[1] = 8.0 * n_int + 4.0 * n_c;
                 out[3] = (c->nu1 * sw_flops + res_flops) * n_int + 8.0 * n_c;
                 break;
-            case 1:  // read omega32 (stencil), psi32, omega64, W0; write omega64 and its shadow
-                out[1] = 36.0 * n_int;
-                out[2] = 5.0 * n_int;
-                out[3] = (c->advect ? 22.0 : 8.0) * n_int;
+            case 1:
+                if (c->rhs64) {  // as the FP64 path: read omega^(1), psi, omega^n; write omega^(2)
+                    out[1] = 32.0 * n_int;
+                    out[2] = (c->advect ? 27.0 : 13.0) * n_int;
+                } else {  // read omega32 (stencil), psi32, omega64, W0; write omega64 and its shadow
+                    out[1] = 36.0 * n_int;
+                    out[2] = 5.0 * n_int;
+                    out[3] = (c->advect ? 22.0 : 8.0) * n_int;
+                }
                 break;
             case 2:  // read psi64, g64; write r32
                 out[1] = 20.0 * n_int;

@@ -412,7 +412,7 @@ size_t cluster_smem_bytes(int N0, int nl, int C, int split, int elem);
 template <typename T>
 cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg, T *psi_out, int Po, int N0, int nl,
                                   int nu1, int nu2, int nuc, T beta, int C, int split);
-int coarse_cluster_size();  // 16, 8, or 0 (device cannot run it, or before init_mg_kernel_attributes)
+int coarse_cluster_size(int device);  // 16, 8, or 0 (device cannot run it, or before init_mg_kernel_attributes on it)
 
 constexpr size_t kMaxSmem = 227 * 1024;
 cudaError_t init_mg_kernel_attributes();

@@ -1101,10 +1101,12 @@ cudaError_t launch_coarse_cluster(cudaStream_t s, int op, const T *g_in, int Pg,
     return cudaLaunchKernelEx(&cfg, k_coarse_cluster<T, 0>, g_in, Pg, psi_out, Po, nu1, nu2, nuc, beta, pl);
 }
 
-// Largest cluster (16, else 8, else 0) that the current device can schedule
-// for the coarse cluster kernel with its largest shared memory; found by
-// init_mg_kernel_attributes (after the non-portable size is allowed).
-static std::atomic<int> g_cluster_size{0};
+// Largest cluster (16, else 8, else 0) that each device can schedule for the
+// coarse cluster kernel with its largest shared memory, by device ordinal;
+// found by init_mg_kernel_attributes with that device current (after the
+// non-portable size is allowed).
+constexpr int kMaxClusterDevices = 64;
+static std::atomic<int> g_cluster_size[kMaxClusterDevices];
 
 static int query_cluster_size() {
     for (int C : {16, 8}) {
@@ -1127,7 +1129,9 @@ static int query_cluster_size() {
     return 0;
 }
 
-int coarse_cluster_size() { return g_cluster_size.load(); }
+int coarse_cluster_size(int device) {
+    return device >= 0 && device < kMaxClusterDevices ? g_cluster_size[device].load() : 0;
+}
 
 namespace {
 
@@ -1243,7 +1247,9 @@ cudaError_t init_mg_kernel_attributes() {
     cudaError_t e = set_attrs_t<double>();
     if (e == cudaSuccess) e = set_cluster_attrs_t<double>();
     if (e == cudaSuccess) e = set_cluster_attrs_t<float>();
-    if (e == cudaSuccess) g_cluster_size.store(query_cluster_size());
+    int dev = -1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && dev >= 0 && dev < kMaxClusterDevices) g_cluster_size[dev].store(query_cluster_size());
     if (e == cudaSuccess) e = set_attrs_t<float>();
     if (e == cudaSuccess) e = set_batch_attrs_t<0>();
     if (e == cudaSuccess) e = set_batch_attrs_t<1>();

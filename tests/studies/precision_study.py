@@ -7,12 +7,13 @@ FP64 oracle at 1e-10 by the parity tests.  Reported per Re: the relative
 max-norm error max|x - x_fp64| / max|x_fp64| of psi, omega, the vertical
 centreline u(y) at x = 1/2 and the horizontal centreline v(x) at y = 1/2
 (central differences of psi, Eq. (22); wall values by the boundary
-conditions), and both paths' step times.  The mixed runs go through the
+conditions), and each path's time per step.  The mixed runs go through the
 batched engine (all Re in one launch per step), which gives the bits of
-single-cavity mixed runs, once with the FP32 L(omega) stencils (the default)
-and once with L(omega) in FP64 (option rhs64).
+single-cavity mixed runs, once in the default form (L(omega) in FP64, option
+rhs64 = 1; FP32 multigrid corrections) and once with L(omega) in FP32 from
+the FP32 shadows of psi and omega (rhs64 = 0).
 
-    python -m tests.studies.precision_study --steps 20000 [--N 1024] > precision.json
+    python -m tests.studies.precision_study --steps 20000 [--N 1024] [--out precision.json]
 """
 import argparse
 import json
@@ -47,25 +48,27 @@ def main():
     ap.add_argument("--N", type=int, default=1024)
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--Re", type=float, nargs="*", default=[5000.0, 10000.0, 20000.0, 30000.0])
+    ap.add_argument("--out", default=None)
     args = ap.parse_args()
     import torch
 
     from paper_0809_3098_gb300 import lc
 
     torch.cuda.set_device(0)
-    out = {"N": args.N, "steps": args.steps, "tol": 1e-10, "results": []}
+    out = {"command": "python -m tests.studies.precision_study " + " ".join(sys.argv[1:]),
+           "N": args.N, "steps": args.steps, "tol": 1e-10, "results": []}
     t0 = time.perf_counter()
     batch = lc.Batch([args.N] * len(args.Re), args.Re)
     batch.step(args.steps)
     batch.synchronize()
     t_mixed = time.perf_counter() - t0
-    # the same with L(omega) in FP64 (option rhs64): separates the error of
-    # the FP32 stencils from that of the FP32 multigrid corrections
+    # the same with L(omega) in FP32 (rhs64 = 0): separates the error of the
+    # FP32 stencils from that of the FP32 multigrid corrections
     t0 = time.perf_counter()
-    batch64 = lc.Batch([args.N] * len(args.Re), args.Re, rhs64=1)
-    batch64.step(args.steps)
-    batch64.synchronize()
-    t_mixed64 = time.perf_counter() - t0
+    batch32 = lc.Batch([args.N] * len(args.Re), args.Re, rhs64=0)
+    batch32.step(args.steps)
+    batch32.synchronize()
+    t_mixed32 = time.perf_counter() - t0
     for c, Re in enumerate(args.Re):
         t1 = time.perf_counter()
         ref = lc.Cavity(args.N, Re, monitor=1)
@@ -81,24 +84,31 @@ def main():
         t_fp64 = time.perf_counter() - t1
         p64, w64 = ref.psi(), ref.omega()
         pm, wm = batch.psi(c), batch.omega(c)
-        pr, wr = batch64.psi(c), batch64.omega(c)
+        pr, wr = batch32.psi(c), batch32.omega(c)
         u64, v64 = centrelines(p64)
         um, vm = centrelines(pm)
         ur, vr = centrelines(pr)
         row = {"Re": Re, "dt": ref.params["dt"], "t_end": ref.params["dt"] * args.steps,
                "rel_err": {"psi": rel(pm, p64), "omega": rel(wm, w64), "u_centre": rel(um, u64),
                            "v_centre": rel(vm, v64)},
-               "rel_err_rhs64": {"psi": rel(pr, p64), "omega": rel(wr, w64), "u_centre": rel(ur, u64),
-                                 "v_centre": rel(vr, v64)},
-               "psi_min": float(p64.min()), "fp64_seconds": t_fp64, "fp64_monitors": monitors,
+               "rel_err_fp32_L": {"psi": rel(pr, p64), "omega": rel(wr, w64), "u_centre": rel(ur, u64),
+                                  "v_centre": rel(vr, v64)},
+               "psi_min": float(p64.min()), "fp64_ms_per_step": 1e3 * t_fp64 / args.steps,
+               "fp64_monitors": monitors,
                "vcycles_per_solve": {"fp64": float(ref.cycle_log().mean()),
-                                     "mixed": float(batch.cycle_log(c).mean())}}
+                                     "mixed": float(batch.cycle_log(c).mean()),
+                                     "mixed_fp32_L": float(batch32.cycle_log(c).mean())}}
         out["results"].append(row)
         ref.close()
         print(json.dumps(row), file=sys.stderr, flush=True)
-    out["mixed_batch_seconds"] = t_mixed
-    out["mixed_rhs64_batch_seconds"] = t_mixed64
-    print(json.dumps(out))
+    n = len(args.Re)
+    out["mixed_batch_ms_per_step"] = {"cavities": n, "default": 1e3 * t_mixed / args.steps,
+                                      "fp32_L": 1e3 * t_mixed32 / args.steps}
+    text = json.dumps(out)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(text + "\n")
+    print(text)
 
 
 if __name__ == "__main__":

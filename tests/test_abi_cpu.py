@@ -115,3 +115,16 @@ def test_batch_options_validate_without_gpu(L):
     bad_N = (ctypes.c_int * 1)(100)
     assert not L.lc_batch_create(1, bad_N, Re, None, 1e-10, lc.LC_PREC_MIXED)
     assert not L.lc_batch_create(2, N, Re, None, 1e-10, lc.LC_PREC_FP64)
+
+
+def test_noalloc_monitor_rejects_bad_arguments_on_the_host(L):
+    """lc_monitor_noalloc checks its sizes and pointers before any CUDA call,
+    so these run without a device; the pointers are never dereferenced."""
+    p = 4096  # a non-NULL address that no check reads
+    assert lc.lc_monitor_noalloc(lc.LC_NOALLOC_MAX_N + 1, p, p, p, p, 10**5, 1.0, p) == lc.LC_ERR_SIZE
+    assert "LC_NOALLOC_MAX_N" in lc.last_error()
+    assert lc.lc_monitor_noalloc(8, p, p, p, p, 8, 1.0, p) == lc.LC_ERR_ARG  # pitch < N + 1
+    assert lc.lc_monitor_noalloc(8, 0, p, p, p, 9, 1.0, p) == lc.LC_ERR_ARG  # NULL array
+    assert lc.lc_monitor_noalloc(8, p, p, p, p, 9, 1.0, 0) == lc.LC_ERR_ARG  # NULL output
+    assert lc.lc_monitor_noalloc(8, p, p, p, p, 9, 0.0, p) == lc.LC_ERR_ARG  # dt <= 0
+    assert lc.lc_monitor_noalloc(0, p, p, p, p, 9, 1.0, p) == lc.LC_ERR_ARG  # N < 1

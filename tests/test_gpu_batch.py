@@ -143,3 +143,27 @@ def test_batch_of_256_cavities_the_maximum():
     for c in (0, 255):
         ref = singles([Ns[c]], [Res[c]], 1)[0]
         assert np.array_equal(b.psi(c), ref[0]) and np.array_equal(b.omega(c), ref[1])
+
+
+@pytest.mark.parametrize("rhs64", [1, 0])
+def test_batch_cavities_beside_the_oracle(rhs64):
+    """A three-cavity batch (N = 128, 256, 384; Re 1000, 5000, 20000) after
+    10 steps from rest, each cavity directly against the FP64 oracle."""
+    import oracle
+    from paper_0809_3098_gb300.workloads import dt_rule
+
+    Ns, Res, steps = [128, 256, 384], [1000.0, 5000.0, 20000.0], 10
+    b = lc.Batch(Ns, Res, rhs64=rhs64)
+    b.step(steps)
+    oracle.set_threads(8)
+    try:
+        for c, (N, Re) in enumerate(zip(Ns, Res)):
+            r = oracle.Cavity(N, Re, dt_rule(N, Re), 1e-10)
+            assert r.step(steps) == oracle.OK
+            rp, rw = r.psi(), r.omega()
+            ep = np.abs(b.psi(c) - rp).max() / np.abs(rp).max()
+            ew = np.abs(b.omega(c) - rw).max() / np.abs(rw).max()
+            assert ep < 1e-6 and ew < 1e-6, (c, ep, ew)
+            r.close()
+    finally:
+        oracle.set_threads(1)

@@ -52,13 +52,27 @@ def test_noalloc_monitor_matches_lc_monitor_on_two_calls():
         assert np.allclose(got, refs[k], rtol=1e-12, atol=0), (k, got, refs[k])
 
 
-def test_noalloc_monitor_rejects_bad_sizes():
+def test_noalloc_monitor_at_the_largest_size():
+    """N = LC_NOALLOC_MAX_N, the size the fixed scratch holds, on device states
+    with a known answer: psi1 - psi0 = 2^-10 everywhere, omega1 - omega0 =
+    j / 8 on row j.  Every sum is exact in FP64, so the monitors are too."""
     import torch
 
-    x = torch.zeros(4, dtype=torch.float64, device="cuda")
-    p = x.data_ptr()
-    assert lc.lc_monitor_noalloc(lc.LC_NOALLOC_MAX_N + 1, p, p, p, p, 10**5, 1.0, p) == lc.LC_ERR_SIZE
-    assert "LC_NOALLOC_MAX_N" in lc.last_error()
-    assert lc.lc_monitor_noalloc(8, p, p, p, p, 8, 1.0, p) == lc.LC_ERR_ARG  # pitch < N + 1
-    assert lc.lc_monitor_noalloc(8, 0, p, p, p, 9, 1.0, p) == lc.LC_ERR_ARG
-    assert lc.lc_monitor_noalloc(8, p, p, p, p, 9, 0.0, p) == lc.LC_ERR_ARG
+    N = lc.LC_NOALLOC_MAX_N
+    n = N + 1
+    dt = 0.5
+    psi0 = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    psi1 = torch.full((n, n), 2.0 ** -10, dtype=torch.float64, device="cuda")
+    w0 = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    w1 = (torch.arange(n, dtype=torch.float64, device="cuda") / 8.0)[:, None].expand(n, n).contiguous()
+    out = torch.full((3,), -1.0, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(2):  # the shared counter and partials must be reset between calls
+        rc = lc.lc_monitor_noalloc(N, psi0.data_ptr(), psi1.data_ptr(), w0.data_ptr(), w1.data_ptr(), n, dt,
+                                   out.data_ptr(), stream.cuda_stream)
+        assert rc == lc.LC_OK, lc.last_error()
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        want = [N / 8.0 / dt, n * 2.0 ** -10, n * (N * (N + 1) / 2) / 8.0 / n]
+        assert got.tolist() == want, (got, want)
+        out.fill_(-1.0)
