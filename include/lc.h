@@ -18,7 +18,9 @@
  *     update of Eq. (15) in colour order (red-black for the 5-point operator,
  *     four colours (i mod 2, j mod 2) for the compact one), until
  *     ||f - L_h psi||_2 <= tol * ||f||_2 over interior nodes (checked after
- *     every cycle, at least one cycle per solve);
+ *     every cycle, at least one cycle per solve); the V-cycle ends at the
+ *     first level below the fine one with at most 16 intervals, whose
+ *     equation is solved exactly (option "coarse_direct");
  *   - steady-state monitors RES_psi, RES_omega, Sec. 3.2, Eqs. (26)-(27).
  *
  * Grid and layout.  N is the number of intervals per side (h = 1/N); fields
@@ -110,7 +112,12 @@ const char *lc_last_error(void);
  *   "op"          LC_OP_5PT or LC_OP_COMPACT (default)       [before first use]
  *   "precision"   LC_PREC_FP64 (default) or LC_PREC_MIXED   [before first use]
  *   "nu1","nu2"   pre/post smoothing sweeps per level (2, 1), 1..16
- *   "nuc"         sweeps on the coarsest grid (16), 1..256
+ *   "coarse_direct" 1 (default): the V-cycle ends at the first level below
+ *                 the fine one with at most 16 intervals and solves that
+ *                 level's equation exactly (2-D sine transform); 0: it goes
+ *                 down to the coarsest level (2, 3, 5 or 7 intervals) and
+ *                 smooths it nuc times
+ *   "nuc"         sweeps on the coarsest grid with coarse_direct = 0 (16), 1..256
  *   "beta"        relaxation of the SOR update, Eq. (15) (1.0), 0 < beta < 2
  *   "max_cycles"  cycle cap per solve (100); hitting it raises LC_ERR_NOCONV
  *   "solver"      0 (default) multigrid V-cycles; 1 the paper's SOR iteration
@@ -233,7 +240,8 @@ int lc_cycle_log(lc_ctx *ctx, int *out, size_t max, size_t *n_out);
 int lc_synchronize(lc_ctx *ctx);
 
 /* Reads back the resolved parameters: out[0] = N, out[1] = Re, out[2] = dt,
- * out[3] = tol, out[4] = h, out[5] = multigrid levels, out[6] = steps taken. */
+ * out[3] = tol, out[4] = h, out[5] = levels the V-cycle visits, out[6] =
+ * steps taken. */
 int lc_get_params(lc_ctx *ctx, double out[7]);
 
 /* Kernel launches the context enqueues: out[0] per step outside the Poisson
@@ -290,7 +298,7 @@ typedef struct lc_batch lc_batch;
 lc_batch *lc_batch_create(int count, const int *N, const double *Re, const double *dt, double tol, int precision);
 void lc_batch_destroy(lc_batch *b);
 
-/* Options as lc_set_option: "op", "coarse_max" (8..64) [before first use],
+/* Options as lc_set_option: "op", "coarse_max" (8..64), "coarse_direct" [before first use],
  * "nu1", "nu2" (1..4), "nuc", "beta", "max_cycles", "U", "advect", "rhs64",
  * "pdl", "graph". */
 int lc_batch_set_option(lc_batch *b, const char *key, double value);
@@ -313,7 +321,7 @@ int lc_batch_set_state(lc_batch *b, int cavity, const double *psi, const double 
 int lc_batch_cycle_log(lc_batch *b, int cavity, int *out, size_t max, size_t *n_out);
 int lc_batch_synchronize(lc_batch *b);
 
-/* out[0] = N, out[1] = Re, out[2] = dt, out[3] = multigrid levels, out[4] =
+/* out[0] = N, out[1] = Re, out[2] = dt, out[3] = levels the V-cycle visits, out[4] =
  * first level of the one-block coarse cycle, out[5] = steps taken, out[6] =
  * tile shape of level 0, out[7] = workspace bytes. */
 int lc_batch_info(lc_batch *b, int cavity, double out[8]);

@@ -71,6 +71,10 @@ def lib():
         L.or_prolong_add.argtypes = [ci, _dp, _dp]
         L.or_poisson_solve.argtypes = [ci, ci, _dp, _dp, cd, ci, ci, ci, cd, _dp]
         L.or_poisson_solve.restype = ci
+        L.or_poisson_solve2.argtypes = [ci, ci, _dp, _dp, cd, ci, ci, ci, cd, ci, _dp]
+        L.or_poisson_solve2.restype = ci
+        L.or_direct_solve.argtypes = [ci, ci, _dp, _dp]
+        L.or_direct_solve.restype = ci
         L.or_thom.argtypes = [ci, cd, ci, _dp, _dp]
         L.or_rhs_L.argtypes = [ci, cd, ci, _dp, _dp, _dp]
         L.or_monitors.argtypes = [ci, cd, _dp, _dp, _dp, _dp, _dp]
@@ -205,13 +209,25 @@ def prolong_add(Nc: int, e, psi) -> np.ndarray:
 
 
 def poisson_solve(N: int, op: int, f, psi0=None, tol: float = 1e-10, max_cycles: int = 100,
-                  nu1: int = 2, nu2: int = 2, beta: float = 1.0):
-    """Multigrid solve of L_h psi = f (reading R7).  Returns (psi, cycles, rel)."""
+                  nu1: int = 2, nu2: int = 2, beta: float = 1.0, direct: int = 1):
+    """Multigrid solve of L_h psi = f (reading R7).  direct = 1 solves the
+    first level below the finest with at most 16 intervals exactly (R15),
+    0 smooths the coarsest level (R12).  Returns (psi, cycles, rel)."""
     psi = _field(N) if psi0 is None else _f64(psi0).copy()
     rel = ctypes.c_double(0.0)
-    cycles = lib().or_poisson_solve(N, op, _p(_f64(f)), _p(psi), tol, max_cycles, nu1, nu2, beta,
-                                    ctypes.byref(rel))
+    cycles = lib().or_poisson_solve2(N, op, _p(_f64(f)), _p(psi), tol, max_cycles, nu1, nu2, beta, int(direct),
+                                     ctypes.byref(rel))
     return psi, cycles, rel.value
+
+
+def direct_solve(n: int, op: int, f) -> np.ndarray:
+    """Exact solve of L_h psi = f on an n-interval grid (the coarse solve of
+    reading R15): dense -L_h built from the operator, Cholesky, substitution."""
+    psi = _field(n)
+    rc = lib().or_direct_solve(n, op, _p(_f64(f)), _p(psi))
+    if rc != OK:
+        raise ValueError(f"or_direct_solve({n}) failed: {rc}")
+    return psi
 
 
 def thom(N: int, psi, omega, U: float = 1.0, profile: int = 0) -> np.ndarray:

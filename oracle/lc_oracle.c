@@ -49,6 +49,10 @@
  *       five solves and the next step's first stage reuses it.
  *   R12 multigrid halves a level while its interval count is even and >= 4;
  *       the coarsest level (2, 3, 5 or 7 intervals) gets nuc smoothing sweeps.
+ *   R15 with the option coarse_direct (default on) the V-cycle instead ends
+ *       at the first level below the finest with at most 16 intervals, where
+ *       the level's equation is solved exactly (a direct solve of the dense
+ *       system; at most 225 unknowns).
  *   R13 the alternative solver "SOR" is Eq. (15) on its own, swept in the
  *       order its n / n+1 superscripts fix (i outer, j inner), with the
  *       stopping test of R7 after every sor_sweeps sweeps.
@@ -304,6 +308,89 @@ static double interior_norm2(int N, const double *x) {
     return sqrt(s);
 }
 
+static size_t nodes_of(int n) { return (size_t)(n + 1) * (n + 1); }
+
+/* ------------------------------------------------------------------------ */
+/* Exact solve of L_h psi = f on one grid of n intervals (reading R15).  The
+ * matrix M = -L_h of the (n-1)^2 interior unknowns (numbered i - 1 + (j - 1)
+ * (n - 1)) is built column by column by applying or_apply_operator to unit
+ * vectors; it is symmetric positive definite, so it is factorised once as
+ * M = G G^T (Cholesky, G lower triangular, row-major in chol[]), and each
+ * solve is the forward substitution G y = -f followed by the back
+ * substitution G^T psi = y. */
+typedef struct {
+    int n, op, m2;
+    double *chol;
+} or_direct;
+
+static int direct_init(or_direct *d, int n, int op) {
+    int m = n - 1, m2 = m * m;
+    d->n = n;
+    d->op = op;
+    d->m2 = m2;
+    d->chol = calloc((size_t)m2 * m2, sizeof(double));
+    double *e = calloc(nodes_of(n), sizeof(double)), *Le = calloc(nodes_of(n), sizeof(double));
+    double *M = d->chol;
+    for (int k = 0; k < m2; ++k) {
+        e[AT(n, 1 + k % m, 1 + k / m)] = 1.0;
+        or_apply_operator(n, op, e, Le);
+        e[AT(n, 1 + k % m, 1 + k / m)] = 0.0;
+        for (int r = 0; r < m2; ++r) M[(size_t)r * m2 + k] = -Le[AT(n, 1 + r % m, 1 + r / m)];
+    }
+    free(e);
+    free(Le);
+    /* Cholesky in place: column by column, G[k][k] = sqrt(M[k][k] - sum G[k][q]^2),
+     * G[r][k] = (M[r][k] - sum G[r][q] G[k][q]) / G[k][k] for r > k. */
+    for (int k = 0; k < m2; ++k) {
+        double dk = M[(size_t)k * m2 + k];
+        for (int q = 0; q < k; ++q) dk -= M[(size_t)k * m2 + q] * M[(size_t)k * m2 + q];
+        if (!(dk > 0.0)) return OR_ERR_ARG;
+        dk = sqrt(dk);
+        M[(size_t)k * m2 + k] = dk;
+        for (int r = k + 1; r < m2; ++r) {
+            double v = M[(size_t)r * m2 + k];
+            for (int q = 0; q < k; ++q) v -= M[(size_t)r * m2 + q] * M[(size_t)k * m2 + q];
+            M[(size_t)r * m2 + k] = v / dk;
+        }
+        for (int c = k + 1; c < m2; ++c) M[(size_t)k * m2 + c] = 0.0;
+    }
+    return OR_OK;
+}
+
+static void direct_free(or_direct *d) {
+    free(d->chol);
+    d->chol = NULL;
+}
+
+/* psi = L_h^{-1} f at interior nodes (walls of psi untouched). */
+static void direct_solve(const or_direct *d, const double *f, double *psi) {
+    int n = d->n, m = n - 1, m2 = d->m2;
+    const double *G = d->chol;
+    double *y = malloc(sizeof(double) * m2);
+    for (int r = 0; r < m2; ++r) {
+        double v = -f[AT(n, 1 + r % m, 1 + r / m)];
+        for (int q = 0; q < r; ++q) v -= G[(size_t)r * m2 + q] * y[q];
+        y[r] = v / G[(size_t)r * m2 + r];
+    }
+    for (int r = m2 - 1; r >= 0; --r) {
+        double v = y[r];
+        for (int q = r + 1; q < m2; ++q) v -= G[(size_t)q * m2 + r] * y[q];
+        y[r] = v / G[(size_t)r * m2 + r];
+    }
+    for (int r = 0; r < m2; ++r) psi[AT(n, 1 + r % m, 1 + r / m)] = y[r];
+    free(y);
+}
+
+/* Stand-alone exact solve for the pins. */
+int or_direct_solve(int n, int op, const double *f, double *psi) {
+    if (n < 2 || n > 64) return OR_ERR_ARG;
+    or_direct d;
+    int st = direct_init(&d, n, op);
+    if (st == OR_OK) direct_solve(&d, f, psi);
+    direct_free(&d);
+    return st;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometric multigrid.  Level 0 is the fine grid; a level is halved while its
  * interval count is even and at least 4, so the coarsest level has 2, 3, 5 or
@@ -318,11 +405,16 @@ typedef struct {
 } or_level;
 
 /* solver OR_SOLVER_MG: one "cycle" is a V(nu1, nu2) cycle; OR_SOLVER_SOR:
- * one "cycle" is sor_sweeps lexicographic SOR sweeps on the fine grid. */
+ * one "cycle" is sor_sweeps lexicographic SOR sweeps on the fine grid.
+ * ldir: the level solved exactly (reading R15), -1 if none (then the V-cycle
+ * goes down to the coarsest level and smooths there). */
+#define OR_DIRECT_MAX 16
+
 typedef struct {
-    int op, nlev, nu1, nu2, nuc, solver, sor_sweeps;
+    int op, nlev, nu1, nu2, nuc, solver, sor_sweeps, ldir;
     double beta;
     or_level lev[OR_MAX_LEVELS];
+    or_direct dir;
 } or_mg;
 
 static int mg_level_count(int N) {
@@ -332,6 +424,19 @@ static int mg_level_count(int N) {
         ++n;
     }
     return (N == 2 || N == 3 || N == 5 || N == 7) ? n : -1;
+}
+
+/* Turns the exact coarse solve of reading R15 on or off. */
+static int mg_set_direct(or_mg *mg, int on) {
+    if (mg->ldir >= 0) direct_free(&mg->dir);
+    mg->ldir = -1;
+    if (!on) return OR_OK;
+    for (int l = 1; l < mg->nlev; ++l)
+        if (mg->lev[l].N <= OR_DIRECT_MAX) {
+            mg->ldir = l;
+            return direct_init(&mg->dir, mg->lev[l].N, mg->op);
+        }
+    return OR_OK;
 }
 
 static int mg_init(or_mg *mg, int N, int op) {
@@ -353,10 +458,12 @@ static int mg_init(or_mg *mg, int N, int op) {
         mg->lev[l].f = l == 0 ? NULL : calloc(m, sizeof(double));
         mg->lev[l].r = calloc(m, sizeof(double));
     }
-    return OR_OK;
+    mg->ldir = -1;
+    return mg_set_direct(mg, 1);
 }
 
 static void mg_free(or_mg *mg) {
+    if (mg->ldir >= 0) direct_free(&mg->dir);
     for (int l = 0; l < mg->nlev; ++l) {
         if (l > 0) {
             free(mg->lev[l].psi);
@@ -368,6 +475,10 @@ static void mg_free(or_mg *mg) {
 
 static void vcycle(or_mg *mg, int l) {
     or_level *L = &mg->lev[l];
+    if (l == mg->ldir) {
+        direct_solve(&mg->dir, L->f, L->psi);
+        return;
+    }
     if (l == mg->nlev - 1) {
         or_smooth(L->N, mg->op, L->psi, L->f, mg->beta, mg->nuc);
         return;
@@ -417,11 +528,13 @@ static int mg_solve(or_mg *mg, double *psi, double *f, double tol, int max_cycle
     return cycles;
 }
 
-/* Stand-alone Poisson solve for the pins: L_h psi = f on an N-interval grid. */
-int or_poisson_solve(int N, int op, const double *f, double *psi, double tol, int max_cycles, int nu1, int nu2,
-                     double beta, double *rel_out) {
+/* Stand-alone Poisson solve for the pins: L_h psi = f on an N-interval grid;
+ * direct = 1 solves the first level below the finest with at most 16
+ * intervals exactly (R15), 0 smooths the coarsest level (R12). */
+int or_poisson_solve2(int N, int op, const double *f, double *psi, double tol, int max_cycles, int nu1, int nu2,
+                      double beta, int direct, double *rel_out) {
     or_mg mg;
-    if (mg_init(&mg, N, op) != OR_OK) return OR_ERR_ARG;
+    if (mg_init(&mg, N, op) != OR_OK || mg_set_direct(&mg, direct) != OR_OK) return OR_ERR_ARG;
     mg.nu1 = nu1;
     mg.nu2 = nu2;
     mg.beta = beta;
@@ -435,6 +548,11 @@ int or_poisson_solve(int N, int op, const double *f, double *psi, double tol, in
     free(fc);
     mg_free(&mg);
     return status == OR_OK ? cycles : status;
+}
+
+int or_poisson_solve(int N, int op, const double *f, double *psi, double tol, int max_cycles, int nu1, int nu2,
+                     double beta, double *rel_out) {
+    return or_poisson_solve2(N, op, f, psi, tol, max_cycles, nu1, nu2, beta, 1, rel_out);
 }
 
 /* Stand-alone lexicographic SOR solve for the pins: passes of sweeps_per_check
@@ -612,7 +730,8 @@ void or_destroy(void *p) {
 }
 
 /* Options: "U", "profile", "advect", "max_cycles", "nu1", "nu2", "nuc",
- * "beta", "solver" (0 multigrid, 1 lexicographic SOR), "sor_sweeps".
+ * "beta", "solver" (0 multigrid, 1 lexicographic SOR), "sor_sweeps",
+ * "coarse_direct" (1 default: reading R15; 0: reading R12).
  * Changing the lid re-applies Thom to the current psi. */
 int or_set_option(void *p, const char *key, double value) {
     or_cavity *cv = (or_cavity *)p;
@@ -629,6 +748,7 @@ int or_set_option(void *p, const char *key, double value) {
     else if (!strcmp(key, "beta")) cv->mg.beta = value;
     else if (!strcmp(key, "solver")) cv->mg.solver = (int)value;
     else if (!strcmp(key, "sor_sweeps")) cv->mg.sor_sweeps = (int)value;
+    else if (!strcmp(key, "coarse_direct")) return mg_set_direct(&cv->mg, (int)value);
     else return OR_ERR_ARG;
     return OR_OK;
 }

@@ -152,6 +152,7 @@ struct lc_ctx {
     int use_graph = 1;
     double beta = 1.0, U = 1.0;
     int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR
+    int coarse_direct = 1;  // the V-cycle ends at the first level below the fine one with <= 16 intervals, solved exactly
     int rhs64 = 1;  // mixed precision: L(omega) in FP64 (0: from the FP32 shadows)
     int fused = 0;                 // 1: fine-level FP64 colour phases of a pass in one cooperative launch
     int barrier_extra = 0;         // test hook: the fused kernel's barrier waits for this many more blocks
@@ -217,6 +218,25 @@ void release_graph(lc_ctx *c) {
     c->graph_dirty = true;
 }
 
+// The level the V-cycle solves exactly: the first level below the fine one
+// with at most 16 intervals (option coarse_direct), or -1 when the V-cycle
+// goes down to the coarsest level (2, 3, 5 or 7 intervals) and smooths it.
+constexpr int kDirectMaxN = 16;
+int direct_level(const lc_ctx *c) {
+    if (!c->coarse_direct) return -1;
+    for (int l = 1; l < c->lay.nlev; ++l)
+        if (c->lay.Nl[l] <= kDirectMaxN) return l;
+    return -1;
+}
+
+// Levels the V-cycle visits, and the sweeps of its last level (0: the exact
+// solve of the multigrid kernels' direct_level).
+int vlevels(const lc_ctx *c) {
+    int ld = direct_level(c);
+    return ld >= 0 ? ld + 1 : c->lay.nlev;
+}
+int last_sweeps(const lc_ctx *c) { return direct_level(c) >= 0 ? 0 : c->nuc; }
+
 // Blocks of the coarse cluster kernel; by default it runs in FP64 only (the
 // FP32 one-block V-cycle is faster than the cluster's barriers).
 int cluster_size(const lc_ctx *c) {
@@ -230,8 +250,8 @@ bool cluster_coarse(const lc_ctx *c, int lc) {
     int C = cluster_size(c), elem = c->mixed() ? 4 : 8;
     int cmax = c->cluster_max > 0 ? c->cluster_max : 128;
     const Layout &L = c->lay;
-    return C > 0 && lc >= 1 && L.Nl[lc] <= cmax && L.Nl[lc] > c->cluster_split &&
-           cluster_smem_bytes(L.Nl[lc], L.nlev - lc, C, c->cluster_split, elem) <= kMaxSmem - 1024;
+    return C > 0 && lc >= 1 && lc + 1 < vlevels(c) && L.Nl[lc] <= cmax && L.Nl[lc] > c->cluster_split &&
+           cluster_smem_bytes(L.Nl[lc], vlevels(c) - lc, C, c->cluster_split, elem) <= kMaxSmem - 1024;
 }
 
 // First level handled by the coarse V-cycle kernel: the first level below the
@@ -240,13 +260,14 @@ bool cluster_coarse(const lc_ctx *c, int lc) {
 // memory.
 int coarse_level(const lc_ctx *c) {
     const Layout &L = c->lay;
+    const int nv = vlevels(c);
     int elem = c->mixed() ? 4 : 8;
-    for (int l = 1; l < L.nlev; ++l)
+    for (int l = 1; l < nv; ++l)
         if (cluster_coarse(c, l)) return l;
     int cmax = c->coarse_max > 0 ? c->coarse_max : (c->mixed() ? 64 : 32);
-    for (int l = 0; l < L.nlev; ++l)
-        if (L.Nl[l] <= cmax && coarse_smem_bytes(L.Nl[l], L.nlev - l, elem) <= kMaxSmem - 1024) return l;
-    return L.nlev - 1;
+    for (int l = 0; l < nv; ++l)
+        if (L.Nl[l] <= cmax && coarse_smem_bytes(L.Nl[l], nv - l, elem) <= kMaxSmem - 1024) return l;
+    return nv - 1;
 }
 
 int tile_shape(const lc_ctx *c, int l) {
@@ -265,22 +286,29 @@ bool blocked_ok(const lc_ctx *c) {
     return true;
 }
 
+const FinishArgs kNoFinish{0, 0, nullptr, 0, nullptr, 0, 0.0, 0};
+
 // One V-cycle with one launch per colour phase on every level (the plain
 // form; used when blocked = 0 or the tiles would not fit in shared memory).
 int enqueue_vcycle_phases(lc_ctx *c, cudaStream_t s) {
     const Layout &L = c->lay;
+    const int nv = vlevels(c);
     int nc = c->op == LC_OP_COMPACT ? 4 : 2;
-    c->kernels_per_cycle = (L.nlev - 1) * ((c->nu1 + c->nu2) * nc + 2) + 1;
-    for (int l = 0; l + 1 < L.nlev; ++l) {
+    c->kernels_per_cycle = (nv - 1) * ((c->nu1 + c->nu2) * nc + 2) + 1;
+    for (int l = 0; l + 1 < nv; ++l) {
         for (int sw = 0; sw < c->nu1; ++sw)
             for (int col = 0; col < nc; ++col)
                 LC_CUDA(launch_smooth_colour<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], col, c->beta));
         LC_CUDA(launch_residual_restrict<double>(s, c->op, c->psi(l), c->g(l), L.Nl[l], L.Pl[l], c->g(l + 1),
                                                  c->psi(l + 1), L.Pl[l + 1]));
     }
-    int lc = L.nlev - 1;
-    LC_CUDA(launch_coarsest<double>(s, c->op, c->psi(lc), c->g(lc), L.Nl[lc], L.Pl[lc], c->nuc, c->beta));
-    for (int l = L.nlev - 2; l >= 0; --l) {
+    int lc = nv - 1;
+    if (direct_level(c) >= 0)  // the exact solve of the last level, as in the coarse kernels
+        LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], nullptr, c->psi(lc), L.Pl[lc], L.Nl[lc], 1,
+                                      c->nu1, c->nu2, 0, c->beta, nullptr, kNoFinish));
+    else
+        LC_CUDA(launch_coarsest<double>(s, c->op, c->psi(lc), c->g(lc), L.Nl[lc], L.Pl[lc], c->nuc, c->beta));
+    for (int l = nv - 2; l >= 0; --l) {
         LC_CUDA(launch_prolong_correct<double>(s, c->psi(l), L.Nl[l], L.Pl[l], c->psi(l + 1), L.Pl[l + 1]));
         for (int sw = 0; sw < c->nu2; ++sw)
             for (int col = 0; col < nc; ++col)
@@ -338,8 +366,6 @@ FinishArgs finish_args(const lc_ctx *c, int nr, cudaGraphConditionalHandle h) {
     return FinishArgs{1, nr, c->at<double>(L.gpart), L.ngpart, c->ds(), h, c->tol, c->max_cycles};
 }
 
-const FinishArgs kNoFinish{0, 0, nullptr, 0, nullptr, 0, 0.0, 0};
-
 // Enqueues one FP64 V-cycle on stream s.  When the cycle's last kernel writes
 // the fine-level residual partials it also takes the end-of-cycle decision
 // (*norm_done = true); otherwise the caller adds the residual-norm kernel.
@@ -366,11 +392,11 @@ int enqueue_vcycle(lc_ctx *c, cudaStream_t s, bool *norm_done, cudaGraphConditio
     }
     if (cluster_coarse(c, lc))
         LC_CUDA(launch_coarse_cluster<double>(s, c->op, c->g(lc), L.Pl[lc], c->psi(lc), L.Pl[lc], L.Nl[lc],
-                                              L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta, cluster_size(c),
+                                              vlevels(c) - lc, c->nu1, c->nu2, last_sweeps(c), c->beta, cluster_size(c),
                                               c->cluster_split));
     else
         LC_CUDA(launch_coarse<double>(s, c->op, c->g(lc), L.Pl[lc], lc == 0 ? c->psi(0) : nullptr, c->psi(lc),
-                                      L.Pl[lc], L.Nl[lc], L.nlev - lc, c->nu1, c->nu2, c->nuc, c->beta,
+                                      L.Pl[lc], L.Nl[lc], vlevels(c) - lc, c->nu1, c->nu2, last_sweeps(c), c->beta,
                                       lc == 0 ? rpart : nullptr, lc == 0 ? finish_args(c, 1, h) : kNoFinish));
     ++k;
     Correct64 none{nullptr, 0, nullptr, 0};
@@ -406,11 +432,11 @@ int enqueue_vcycle_mixed(lc_ctx *c, cudaStream_t s, cudaGraphConditionalHandle h
                                    c->g32(l + 1), L.Pl[l + 1], c->nu1, beta));
     if (cluster_coarse(c, lc))
         LC_CUDA(launch_coarse_cluster<float>(s, c->op, c->g32(lc), L.Pl[lc], c->eA(lc), L.Pl[lc], L.Nl[lc],
-                                             L.nlev - lc, c->nu1, c->nu2, c->nuc, beta, cluster_size(c),
+                                             vlevels(c) - lc, c->nu1, c->nu2, last_sweeps(c), beta, cluster_size(c),
                                              c->cluster_split));
     else
         LC_CUDA(launch_coarse<float>(s, c->op, c->g32(lc), L.Pl[lc], nullptr, c->eA(lc), L.Pl[lc], L.Nl[lc],
-                                     L.nlev - lc, c->nu1, c->nu2, c->nuc, beta, nullptr, kNoFinish));
+                                     vlevels(c) - lc, c->nu1, c->nu2, last_sweeps(c), beta, nullptr, kNoFinish));
     ++k;
     if (lc == 0) {
         LC_CUDA(launch_correct64(s, c->eA(0), L.Pl[0], c->psi(0), L.Pl[0], nullptr, L.Pl[0], c->N));
@@ -799,6 +825,9 @@ int lc_set_option(lc_ctx *c, const char *key, double v) {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "solver must be 0 (multigrid) or 1 (SOR)");
         if (iv == 1 && c->mixed()) return fail(LC_ERR_ARG, "the SOR solver runs in FP64 precision only");
         c->solver = iv;
+    } else if (k == "coarse_direct") {
+        if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "coarse_direct must be 0 or 1");
+        c->coarse_direct = iv;
     } else if (k == "rhs64") {
         if (!integral || (iv != 0 && iv != 1)) return fail(LC_ERR_ARG, "rhs64 must be 0 or 1");
         c->rhs64 = iv;
@@ -991,7 +1020,7 @@ int lc_get_params(lc_ctx *c, double out[7]) {
     out[2] = c->dt;
     out[3] = c->tol;
     out[4] = 1.0 / c->N;
-    out[5] = c->lay.nlev;
+    out[5] = vlevels(c);
     out[6] = (double)c->steps;
     return LC_OK;
 }

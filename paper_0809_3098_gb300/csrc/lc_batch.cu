@@ -71,6 +71,8 @@ struct BLayout {
 struct lc_batch {
     int count = 0;
     std::vector<int> N, nlev, lc;
+    std::vector<int> nv;  // levels the V-cycle visits (the last one solved exactly with coarse_direct)
+    int coarse_direct = 1;
     std::vector<double> Re, dt;
     double tol = 1e-10, beta = 1.0, U = 1.0;
     int op = LC_OP_COMPACT, nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
@@ -132,11 +134,19 @@ bool plan(lc_batch *b) {
     L = BLayout();
     int C = b->count;
     b->nlev.assign(C, 0);
+    b->nv.assign(C, 0);
     b->lc.assign(C, 0);
     b->Lmax = 0;
     for (int c = 0; c < C; ++c) {
         b->nlev[c] = nlevels(b->N[c]);
-        b->lc[c] = coarse_level_of(b->N[c], b->nlev[c], b->coarse_max);
+        b->nv[c] = b->nlev[c];
+        if (b->coarse_direct)  // the first level below the fine one with at most 16 intervals is solved exactly
+            for (int l = 1; l < b->nlev[c]; ++l)
+                if ((b->N[c] >> l) <= 16) {
+                    b->nv[c] = l + 1;
+                    break;
+                }
+        b->lc[c] = coarse_level_of(b->N[c], b->nv[c], b->coarse_max);
         if (b->lc[c] < 1) return false;  // every cavity has at least one tile level
         if (b->lc[c] > b->Lmax) b->Lmax = b->lc[c];
     }
@@ -178,7 +188,7 @@ bool plan(lc_batch *b) {
         }
         L.log[c] = take(sizeof(int) * kLogN);
         int cl = b->lc[c];
-        size_t cs = coarse_smem_bytes(N >> cl, b->nlev[c] - cl, 4);
+        size_t cs = coarse_smem_bytes(N >> cl, b->nv[c] - cl, 4);
         if (cs > b->coarse_smem) b->coarse_smem = cs;
     }
     L.nranges = 2 + kMaxLevels;  // [0] stage, [1 + l] level-l tiles, [kResRange] residual
@@ -215,9 +225,9 @@ void fill_tables(lc_batch *b) {
         memset(&v, 0, sizeof(v));
         v.active = keep_active;
         v.N = b->N[c];
-        v.nlev = b->nlev[c];
+        v.nlev = b->nv[c];
         v.lc = b->lc[c];
-        for (int l = 0; l < v.nlev; ++l) {
+        for (int l = 0; l < b->nlev[c]; ++l) {
             v.P[l] = pitch32(v.N >> l);
             v.eA[l] = b->at<float>(L.eA[c][l]);
             v.eB[l] = b->at<float>(L.eB[c][l]);
@@ -326,7 +336,8 @@ int enqueue_cycle(lc_batch *b, cudaStream_t s, cudaGraphConditionalHandle h) {
         if (b->rblocks[1 + l])
             LB_CUDA(launch_down_batch<float>(s, shape_of(b, l), b->op, b->dcav(), b->drange(1 + l), l,
                                              b->rblocks[1 + l], b->nu1, beta));
-    LB_CUDA(launch_coarse_batch(s, b->op, b->dcav(), b->count, (int)b->coarse_smem, b->nu1, b->nu2, b->nuc, beta));
+    LB_CUDA(launch_coarse_batch(s, b->op, b->dcav(), b->count, (int)b->coarse_smem, b->nu1, b->nu2,
+                                b->coarse_direct ? 0 : b->nuc, beta));
     for (int l = b->Lmax - 1; l >= 0; --l)
         if (b->rblocks[1 + l])
             LB_CUDA(launch_up_batch<float>(s, shape_of(b, l), b->op, b->dcav(), b->drange(1 + l), l,
@@ -570,11 +581,14 @@ int lc_batch_set_option(lc_batch *b, const char *key, double v) {
     std::string k(key);
     int iv = (int)v;
     bool integral = v == (double)iv;
-    if (k == "op" || k == "coarse_max") {
+    if (k == "op" || k == "coarse_max" || k == "coarse_direct") {
         if (b->initialized) return bfail(LC_ERR_ARG, k + " must be set before first use");
         if (k == "op") {
             if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "op must be 0 or 1");
             b->op = iv;
+        } else if (k == "coarse_direct") {
+            if (!integral || (iv != 0 && iv != 1)) return bfail(LC_ERR_ARG, "coarse_direct must be 0 or 1");
+            b->coarse_direct = iv;
         } else {
             if (!integral || iv < 8 || iv > 64) return bfail(LC_ERR_ARG, "coarse_max must be 8..64");
             b->coarse_max = iv;
@@ -734,7 +748,7 @@ int lc_batch_info(lc_batch *b, int cavity, double out[8]) {
     out[0] = b->N[cavity];
     out[1] = b->Re[cavity];
     out[2] = b->dt[cavity];
-    out[3] = b->nlev[cavity];
+    out[3] = b->nv[cavity];
     out[4] = b->lc[cavity];
     out[5] = (double)b->steps;
     out[6] = b->Lmax > 0 ? shape_of(b, 0) : -1;

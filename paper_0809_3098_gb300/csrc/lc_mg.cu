@@ -28,6 +28,7 @@
 #include <cooperative_groups.h>
 
 #include <atomic>
+#include <cmath>
 
 namespace lcx {
 
@@ -460,6 +461,88 @@ __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Exact solve of the last level of a V-cycle (the coarse solve of the
+// multigrid; nuc = 0 selects it).  In the scaled form the level's equation is
+//     (I - 0.2 N4 - 0.05 D4) psi = g   (compact)     (I - 0.25 N4) psi = g   (5-point)
+// on the m x m interior nodes (m = n - 1), with N4 / D4 the sums of the edge /
+// diagonal neighbours and psi = 0 on the walls.  Both neighbour sums are
+// diagonalised by the 2-D sine transform: with S[a][y] = sqrt(2/n)
+// sin(pi (a+1)(y+1) / n), symmetric and its own inverse, and c_a =
+// cos(pi (a+1) / n), the sine mode (a, b) has N4 = 2 c_a + 2 c_b and
+// D4 = (2 c_a)(2 c_b), so
+//     psi = S ((S G S) ./ lambda) S,   lambda_ab = 1 - 0.2 (2c_a + 2c_b) - 0.05 (2c_a)(2c_b)
+// (5-point: 1 - 0.25 (2c_a + 2c_b)), G the interior g as rows y, columns x.
+// The host computes S and W = 1 / lambda in FP64 for every level size
+// 2 <= n <= kDirectMaxN, for both operators; the FP32 kernels use the same
+// values rounded.  Each output of each of the four m x m products is one
+// thread's FMA chain in index order, so every kernel that solves a level this
+// way gives the same bits.
+constexpr int kDirectMaxN = 16;
+// entries of S, W (5-point) and W (compact) for n = 2 .. kDirectMaxN
+constexpr int kDirectTable = 3 * (kDirectMaxN - 1) * kDirectMaxN * (2 * kDirectMaxN - 1) / 6;
+// scratch of direct_level: S, W and two m x m products
+constexpr int kDirectScratch = 4 * (kDirectMaxN - 1) * (kDirectMaxN - 1);
+
+__device__ double g_direct64[kDirectTable];
+__device__ float g_direct32[kDirectTable];
+
+// Offset of level size n's block (S, W 5-point, W compact) in the tables.
+__host__ __device__ constexpr int direct_off(int n) { return (n - 2) * (n - 1) * (2 * n - 3) / 2; }
+
+template <typename T>
+__device__ __forceinline__ const T *direct_table();
+template <>
+__device__ __forceinline__ const double *direct_table<double>() {
+    return g_direct64;
+}
+template <>
+__device__ __forceinline__ const float *direct_table<float>() {
+    return g_direct32;
+}
+
+template <typename T, int OP>
+__device__ void direct_level(T *sp, const T *sg, int n, T *scr) {
+    if (n < 2 || n > kDirectMaxN) return;  // the host never asks for it: the tables stop at kDirectMaxN
+    const int m = n - 1, LP = n + 1, mm = m * m;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    const T *tab = direct_table<T>() + direct_off(n);
+    T *S = scr, *W = scr + mm, *A = scr + 2 * mm, *B = scr + 3 * mm;
+    for (int q = tid; q < mm; q += nt) {
+        S[q] = tab[q];
+        W[q] = tab[(OP == 1 ? 2 : 1) * mm + q];
+    }
+    __syncthreads();
+    for (int q = tid; q < mm; q += nt) {  // A = S G
+        const int a = q / m, x = q - a * m;
+        T v = T(0);
+        for (int y = 0; y < m; ++y) v = fma(S[a * m + y], sg[(y + 1) * LP + x + 1], v);
+        A[q] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < mm; q += nt) {  // B = (A S) ./ lambda
+        const int a = q / m, b = q - a * m;
+        T v = T(0);
+        for (int x = 0; x < m; ++x) v = fma(A[a * m + x], S[x * m + b], v);
+        B[q] = v * W[q];
+    }
+    __syncthreads();
+    for (int q = tid; q < mm; q += nt) {  // A = S B
+        const int y = q / m, b = q - y * m;
+        T v = T(0);
+        for (int a = 0; a < m; ++a) v = fma(S[y * m + a], B[a * m + b], v);
+        A[q] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < mm; q += nt) {  // psi = A S
+        const int y = q / m, x = q - y * m;
+        T v = T(0);
+        for (int b = 0; b < m; ++b) v = fma(A[y * m + b], S[b * m + x], v);
+        sp[(y + 1) * LP + x + 1] = v;
+    }
+    __syncthreads();
+}
+
 // Full weighting of the residual sr around fine node (2X, 2Y) onto coarse
 // node (X, Y); the coarse correction starts from zero.
 template <typename T>
@@ -490,8 +573,10 @@ __device__ __forceinline__ void prolong_add(T *sp, const T *ec, int LP, int LPc,
 
 // A V-cycle over nl levels held in shared memory from base: psi and g of each
 // level ((n + 1)^2 each, n = N0 >> k), level after level, boundaries zero;
-// sr is residual scratch of (N0 + 1)^2.  psi and g of the top level are set
-// on entry; the coarser levels' psi is reset here.  The whole block runs it.
+// sr is residual scratch of max((N0 + 1)^2, kDirectScratch).  psi and g of the
+// top level are set on entry; the coarser levels' psi is reset here.  The
+// last level gets nuc colour sweeps, or with nuc = 0 its exact solve
+// (direct_level).  The whole block runs it.
 template <typename T, int OP>
 __device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int nu1, int nu2, int nuc, T beta) {
     int tx = threadIdx.x, ty = threadIdx.y, bx = blockDim.x, by = blockDim.y;
@@ -536,8 +621,10 @@ __device__ __forceinline__ void smem_vcycle(T *base, T *sr, int N0, int nl, int 
     {
         int n = N0 >> (nl - 1), LP = n + 1;
         T *sp = base + off, *sg = sp + LP * LP;
-        // with one unknown and beta = 1 a single sweep is already exact
-        cs_sweeps<T, OP>(sp, sg, n, (n == 2 && beta == T(1)) ? 1 : nuc, beta);
+        if (nuc <= 0)
+            direct_level<T, OP>(sp, sg, n, sr);
+        else  // with one unknown and beta = 1 a single sweep is already exact
+            cs_sweeps<T, OP>(sp, sg, n, (n == 2 && beta == T(1)) ? 1 : nuc, beta);
     }
     // up
     for (int k = nl - 2; k >= 0; --k) {
@@ -1025,7 +1112,8 @@ cudaError_t launch_up(cudaStream_t s, int shape, int op, const T *psi_in, const 
 size_t coarse_smem_bytes(int N0, int nl, int elem) {
     size_t n = 0;
     for (int k = 0; k < nl; ++k) n += 2 * (size_t)((N0 >> k) + 1) * ((N0 >> k) + 1);
-    n += (size_t)(N0 + 1) * (N0 + 1);
+    size_t sr = (size_t)(N0 + 1) * (N0 + 1);
+    n += sr > (size_t)kDirectScratch ? sr : (size_t)kDirectScratch;
     return n * elem;
 }
 
@@ -1066,7 +1154,8 @@ static ClusterPlan cluster_plan(int N0, int nl, int C, int split) {
     int single = 0;
     for (int k = pl.nd; k < nl; ++k) single += 2 * ((N0 >> k) + 1) * ((N0 >> k) + 1);
     pl.single = take(single);
-    pl.sr = take(((N0 >> pl.nd) + 1) * ((N0 >> pl.nd) + 1));
+    const int nsr = ((N0 >> pl.nd) + 1) * ((N0 >> pl.nd) + 1);
+    pl.sr = take(nsr > kDirectScratch ? nsr : kDirectScratch);
     pl.zero = take(N0 + 2);
     pl.total = off;
     return pl;
@@ -1243,6 +1332,36 @@ static cudaError_t set_cluster_attrs_t() {
     return cudaSuccess;
 }
 
+// The tables of direct_level for every level size 2 <= n <= kDirectMaxN,
+// computed in FP64 on the host and copied to each device once.
+static std::atomic<bool> g_direct_ready[kMaxClusterDevices];
+
+static cudaError_t init_direct_tables(int dev) {
+    if (dev < 0 || dev >= kMaxClusterDevices) return cudaErrorInvalidDevice;
+    if (g_direct_ready[dev].load()) return cudaSuccess;
+    static double t64[kDirectTable];
+    static float t32[kDirectTable];
+    const double pi = 3.14159265358979323846;
+    for (int n = 2; n <= kDirectMaxN; ++n) {
+        const int m = n - 1, mm = m * m;
+        double *S = t64 + direct_off(n), *W5 = S + mm, *Wc = S + 2 * mm;
+        const double sc = std::sqrt(2.0 / n);
+        for (int a = 0; a < m; ++a)
+            for (int y = 0; y < m; ++y) S[a * m + y] = sc * std::sin(pi * (a + 1) * (y + 1) / n);
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b) {
+                const double ca = 2.0 * std::cos(pi * (a + 1) / n), cb = 2.0 * std::cos(pi * (b + 1) / n);
+                W5[a * m + b] = 1.0 / (1.0 - 0.25 * (ca + cb));
+                Wc[a * m + b] = 1.0 / (1.0 - 0.2 * (ca + cb) - 0.05 * (ca * cb));
+            }
+    }
+    for (int k = 0; k < kDirectTable; ++k) t32[k] = (float)t64[k];
+    cudaError_t e = cudaMemcpyToSymbol(g_direct64, t64, sizeof(t64));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_direct32, t32, sizeof(t32));
+    if (e == cudaSuccess) g_direct_ready[dev].store(true);
+    return e;
+}
+
 cudaError_t init_mg_kernel_attributes() {
     cudaError_t e = set_attrs_t<double>();
     if (e == cudaSuccess) e = set_cluster_attrs_t<double>();
@@ -1250,6 +1369,7 @@ cudaError_t init_mg_kernel_attributes() {
     int dev = -1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess && dev >= 0 && dev < kMaxClusterDevices) g_cluster_size[dev].store(query_cluster_size());
+    if (e == cudaSuccess) e = init_direct_tables(dev);
     if (e == cudaSuccess) e = set_attrs_t<float>();
     if (e == cudaSuccess) e = set_batch_attrs_t<0>();
     if (e == cudaSuccess) e = set_batch_attrs_t<1>();

@@ -55,11 +55,14 @@ def test_dt_rule_and_params(L):
     h = lc.lc_create(1024, 10000.0, 0.0, 1e-10)
     p = lc.lc_get_params(h)
     assert p[2] == 0.25 * min(1 / 1024, 10000.0 / 1024**2 / 4)
-    assert p[5] == 10  # 1024 .. 2
+    assert p[5] == 7  # the V-cycle visits 1024 .. 16 (16 solved exactly)
     lc.lc_destroy(h)
     h = lc.lc_create(384, 1000.0, 1e-3, 1e-10)
     p = lc.lc_get_params(h)
-    assert p[2] == 1e-3 and p[5] == 8  # 384 .. 3
+    assert p[2] == 1e-3 and p[5] == 6  # 384 .. 12 (12 solved exactly)
+    assert lc.lc_set_option(h, "coarse_direct", 0) == lc.LC_OK
+    assert lc.lc_get_params(h)[5] == 8  # 384 .. 3, the coarsest grid smoothed
+    assert lc.lc_set_option(h, "coarse_direct", 2) == lc.LC_ERR_ARG
     lc.lc_destroy(h)
 
 

@@ -167,3 +167,14 @@ def test_batch_cavities_beside_the_oracle(rhs64):
             r.close()
     finally:
         oracle.set_threads(1)
+
+
+def test_batch_smoothed_coarsest_grid_bitwise_equals_single_contexts():
+    """coarse_direct = 0 in the batch and in single contexts: the same bits."""
+    Ns, Res = [128, 224, 320], [2000.0, 9000.0, 15000.0]
+    b = lc.Batch(Ns, Res, coarse_direct=0)
+    b.step(2)
+    ref = singles(Ns, Res, 2, coarse_direct=0)
+    for c, (p, w, cyc) in enumerate(ref):
+        assert np.array_equal(b.cycle_log(c), cyc), c
+        assert np.array_equal(b.psi(c), p) and np.array_equal(b.omega(c), w), c

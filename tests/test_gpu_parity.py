@@ -336,3 +336,31 @@ def test_lid_at_rest_keeps_the_fluid_at_rest(precision):
     g.step(3)
     assert not g.psi().any() and not g.omega().any()
     assert (g.cycle_log() == 1).all()
+
+
+@pytest.mark.parametrize("mode", ["phases", "coarse-block", "cluster16", "cluster3-split8", "tiles"])
+@pytest.mark.parametrize("N", [48, 128, 224])
+def test_smoothed_coarsest_grid_matches_oracle(mode, N):
+    """coarse_direct = 0: the V-cycle goes down to the 2-, 3-, 5- or 7-interval
+    grid and smooths it nuc times (instead of solving the first level of at
+    most 16 intervals exactly); both sides switch together."""
+    dt = dt_rule(N, 800.0)
+    g = lc.Cavity(N, 800.0, dt, 1e-10, coarse_direct=0, **MODES[mode])
+    r = oracle.Cavity(N, 800.0, dt, 1e-10, coarse_direct=0)
+    g.step(3)
+    r.step(3)
+    assert rel(g.psi(), r.psi()) < 1e-12 and rel(g.omega(), r.omega()) < 1e-12
+    assert np.array_equal(g.cycle_log(), r.cycle_log())
+
+
+@pytest.mark.parametrize("N", [32, 96, 160])
+def test_exact_coarse_level_sizes(N):
+    """The exactly solved level is 16, 12 and 10 intervals here (the 2-D sine
+    transform of 15, 11 and 9 unknowns per side); the GPU's transform and the
+    oracle's Cholesky solve agree to rounding and give the same cycle counts."""
+    g, r = pair(N, 1500.0, lc.LC_OP_COMPACT)
+    g.step(3)
+    assert r.step(3) == oracle.OK
+    assert rel(g.psi(), r.psi()) < 1e-12 and rel(g.omega(), r.omega()) < 1e-12
+    assert np.array_equal(g.cycle_log(), r.cycle_log())
+    assert g.params["levels"] == {32: 2, 96: 4, 160: 5}[N]

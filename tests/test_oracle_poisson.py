@@ -198,16 +198,18 @@ def test_restriction_of_constant_and_walls():
     assert np.allclose(fc[1:-1, 1:-1], 2.5, rtol=0, atol=1e-15)
 
 
+@pytest.mark.parametrize("direct", [1, 0])
 @pytest.mark.parametrize("N", [128, 224, 320])
 @pytest.mark.parametrize("op", OPS)
-def test_multigrid_contraction(op, N):
-    """A V(2,2) cycle contracts the residual by at least 5x per cycle, also
-    when the coarsest grid has 7 (224 = 7 * 32) or 5 (320 = 5 * 64) intervals."""
+def test_multigrid_contraction(op, N, direct):
+    """A V(2,2) cycle contracts the residual by at least 5x per cycle, with
+    the exact coarse solve (R15) and with the smoothed coarsest grid (R12),
+    also when that grid has 7 (224 = 7 * 32) or 5 (320 = 5 * 64) intervals."""
     f = random_rhs(N, seed=1)
     psi = np.zeros_like(f)
     prev = np.linalg.norm(f)
     for _ in range(4):
-        psi, cycles, rel = oracle.poisson_solve(N, op, f, psi0=psi, tol=1e-300, max_cycles=1)
+        psi, cycles, rel = oracle.poisson_solve(N, op, f, psi0=psi, tol=1e-300, max_cycles=1, direct=direct)
         r = np.linalg.norm(oracle.residual(N, op, psi, f))
         assert r < 0.2 * prev
         prev = r
@@ -223,3 +225,40 @@ def test_rejects_unsupported_sizes():
     f = np.zeros((37, 37))
     psi, cycles, rel = oracle.poisson_solve(36, OP_5PT, f)   # 36 = 4 * 9
     assert cycles == oracle.ERR_ARG
+
+
+@pytest.mark.parametrize("n", [2, 4, 5, 6, 7, 8, 10, 12, 14, 16])
+@pytest.mark.parametrize("op", OPS)
+def test_direct_coarse_solve_matches_dst(n, op):
+    """The exact coarse solve of reading R15 (dense -L_h, Cholesky) against the
+    independent DST-I solution, and on the discrete eigenvector."""
+    f = random_rhs(n, seed=100 + n + op)
+    ref = dst_solve(n, op, f)
+    psi = oracle.direct_solve(n, op, f)
+    assert np.abs(psi - ref).max() < 1e-13 * np.abs(ref).max()
+    X, Y = grid(n)
+    S = np.sin(np.pi * X) * np.sin(np.pi * Y)
+    h = 1.0 / n
+    m = mu(n)
+    lam = 2 * m if op == OP_5PT else 2 * m + h**2 / 6 * m * m
+    fe = lam * S
+    fe[0] = fe[-1] = 0
+    fe[:, 0] = fe[:, -1] = 0
+    assert np.abs(oracle.direct_solve(n, op, fe) - S).max() < 1e-13
+
+
+@pytest.mark.parametrize("N", [8, 16, 96, 224, 320])
+@pytest.mark.parametrize("op", OPS)
+def test_exact_coarse_level_keeps_the_solution_and_speeds_convergence(N, op):
+    """Both coarsest-level treatments (R15 exact solve at <= 16 intervals,
+    R12 smoothing of the 2/3/5/7-interval grid) reach the DST-I solution; the
+    exact coarse solve never needs more cycles."""
+    f = random_rhs(N, seed=N + 3 * op)
+    ref = dst_solve(N, op, f)
+    out = {}
+    for direct in (1, 0):
+        psi, cycles, rel = oracle.poisson_solve(N, op, f, tol=1e-12, nu1=2, nu2=1, direct=direct)
+        assert rel <= 1e-12 and cycles > 0
+        assert np.abs(psi - ref).max() < 1e-10 * np.abs(ref).max()
+        out[direct] = cycles
+    assert out[1] <= out[0], out
