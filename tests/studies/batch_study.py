@@ -6,7 +6,7 @@ largest and the one with the highest Re) the relative max-norm error against
 an FP64 single-cavity run of the same steps, in psi, omega and the
 centreline velocities.
 
-    python -m tests.studies.batch_study --steps 5000 > batch.json
+    python -m tests.studies.batch_study --steps 5000 [--out batch.json]
 """
 import argparse
 import json
@@ -25,7 +25,8 @@ from tests.studies.precision_study import centrelines, rel  # noqa: E402
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=5000)
-    ap.add_argument("--rhs64", type=int, default=0)
+    ap.add_argument("--rhs64", type=int, default=None, help="L(omega) in FP64 (1, the default) or FP32 (0)")
+    ap.add_argument("--out", default=None)
     args = ap.parse_args()
     import torch
 
@@ -35,7 +36,8 @@ def main():
     torch.cuda.set_device(0)
     cav = batch_cavities(32, seed=0)
     Ns, Res = [n for n, _ in cav], [r for _, r in cav]
-    b = lc.Batch(Ns, Res, rhs64=args.rhs64)
+    opts = {} if args.rhs64 is None else {"rhs64": args.rhs64}
+    b = lc.Batch(Ns, Res, **opts)
     schedule = b.autotune_schedule(steps=2)
     shapes = b.autotune(reps=3)
     nodes = sum((n - 1) ** 2 for n in Ns)
@@ -47,8 +49,10 @@ def main():
     e1.synchronize()
     b.synchronize()
     ms = e0.elapsed_time(e1)
-    out = {"steps": args.steps, "cavities": len(Ns), "interior_nodes": nodes, "schedule": schedule,
-           "tile_shapes": shapes, "rhs64": args.rhs64, "seconds": ms / 1e3,
+    out = {"command": "python -m tests.studies.batch_study " + " ".join(sys.argv[1:]),
+           "steps": args.steps, "cavities": len(Ns), "interior_nodes": nodes, "N": Ns,
+           "Re": [round(r, 1) for r in Res], "schedule": schedule,
+           "tile_shapes": shapes, "rhs64": 1 if args.rhs64 is None else args.rhs64, "seconds": ms / 1e3,
            "updates_per_s": nodes * 5 * args.steps / (ms / 1e3), "checks": []}
     picks = sorted({int(np.argmin(Ns)), int(np.argmax(Ns)), int(np.argmax(Res))})
     for c in picks:
@@ -66,7 +70,11 @@ def main():
         out["checks"].append(row)
         ref.close()
         print(json.dumps(row), file=sys.stderr, flush=True)
-    print(json.dumps(out))
+    text = json.dumps(out)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(text + "\n")
+    print(text)
 
 
 if __name__ == "__main__":

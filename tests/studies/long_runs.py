@@ -17,7 +17,7 @@ periodic flow shows as an oscillating probe.
     python -m tests.studies.long_runs coarse --out coarse.json
         The paper's coarse-grid cases (220^2 read as 224 intervals) at
         Re 10000 under several solver settings: multigrid solved to 1e-10 in
-        mixed precision (and in FP64 with --fp64), the same with dt halved, and the
+        mixed precision at the time steps --mg-dts (and in FP64 with --fp64), and the
         paper's own SOR iteration of Eq. (15) with a fixed budget of sweeps per
         stage (tol so large that every solve stops after one pass) at
         relaxation beta from the paper's 0.8 -> 0.1 range.
@@ -142,14 +142,13 @@ def coarse(args):
     from paper_0809_3098_gb300 import lc
 
     MIXED = lc.LC_PREC_MIXED
-    N, Re, dt = args.N, args.Re, args.dt
-    cases = [Case("multigrid, mixed, dt", N, Re, dt, precision=MIXED),
-             Case("multigrid, mixed, dt/2", N, Re, dt / 2, precision=MIXED)]
+    N, Re = args.N, args.Re
+    cases = [Case(f"multigrid to 1e-10, mixed, dt={dt:g}", N, Re, dt, precision=MIXED) for dt in args.mg_dts]
     if args.fp64:
-        cases.append(Case("multigrid, FP64, dt", N, Re, dt))
+        cases.append(Case(f"multigrid to 1e-10, FP64, dt={args.dt:g}", N, Re, args.dt))
     for beta, sweeps in args.sor:
-        cases.append(Case(f"SOR beta={beta} sweeps/stage={sweeps}", N, Re, dt, tol=1e30, solver=1, beta=beta,
-                          sor_sweeps=sweeps))
+        cases.append(Case(f"SOR beta={beta} sweeps/stage={sweeps}, dt={args.dt:g}", N, Re, args.dt, tol=1e30,
+                          solver=1, beta=beta, sor_sweeps=sweeps))
     run_cases(cases, args.t_end, args.every, args.max_seconds)
     return {"cases": [c.summary() for c in cases]}
 
@@ -175,6 +174,8 @@ def main():
     ap.add_argument("--sor", type=lambda s: tuple(float(x) if "." in x else int(x) for x in s.split(":")),
                     nargs="*", default=[(0.5, 1), (0.5, 10)], help="beta:sweeps per stage")
     ap.add_argument("--fp64", action="store_true", help="coarse: add the FP64 multigrid case")
+    ap.add_argument("--mg-dts", type=float, nargs="*", default=[0.001, 0.0005],
+                    help="coarse: time steps of the multigrid cases")
     ap.add_argument("--max-seconds", type=float, default=1e9)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()

@@ -13,7 +13,7 @@ CPU oracle at full resolution:
   * the steady-state monitors max|d omega|/dt, RES_psi, RES_omega.
 The fields restricted to 257^2 by injection (stride 8) are saved as .npy.
 
-    python -m tests.studies.stress_study --steps 20000 --every 5000 --out DIR
+    python -m tests.studies.stress_study --steps 20000 --every 5000 --out DIR [--summary stress.json]
 """
 import argparse
 import json
@@ -38,6 +38,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20000)
     ap.add_argument("--every", type=int, default=5000)
     ap.add_argument("--out", default="stress_out")
+    ap.add_argument("--summary", default=None, help="also write the JSON summary to this file")
     args = ap.parse_args()
     import torch
 
@@ -91,7 +92,12 @@ def main():
         records.append(rec)
         print(json.dumps(rec), file=sys.stderr, flush=True)
         os.remove(path)
-    print(json.dumps({"N": N, "Re": Re, "dt": dt, "steps": args.steps, "checkpoints": records}))
+    text = json.dumps({"command": "python -m tests.studies.stress_study " + " ".join(sys.argv[1:]),
+                       "N": N, "Re": Re, "dt": dt, "steps": args.steps, "checkpoints": records})
+    if args.summary:
+        with open(args.summary, "w") as f:
+            f.write(text + "\n")
+    print(text)
 
 
 if __name__ == "__main__":
