@@ -476,8 +476,16 @@ __device__ void cs_sweeps(T *sp, const T *sg, int n, int nu, T beta) {
 // The host computes S and W = 1 / lambda in FP64 for every level size
 // 2 <= n <= kDirectMaxN, for both operators; the FP32 kernels use the same
 // values rounded.  Each output of each of the four m x m products is one
-// thread's FMA chain in index order, so every kernel that solves a level this
-// way gives the same bits.
+// thread's FMA chain in a fixed order, so every kernel that solves a level
+// this way gives the same bits.
+//
+// The scheme is exactly equivariant under the mirror x -> 1 - x with
+// psi -> -psi (lid reversal), as the smoother is: the table's rows obey
+// S[m-1-x][b] = (-1)^b S[x][b] bit for bit (the host computes the first half
+// and mirrors it; the middle row of an odd m holds exact zeros and +-sqrt(2/n)),
+// the products along x run with x as the output index, and the one sum over
+// x takes x and m-1-x as a pair, S[x][b] (A[x] +- A[m-1-x]), so a mirrored
+// input gives the same terms in the same order with exact sign flips.
 constexpr int kDirectMaxN = 16;
 // entries of S, W (5-point) and W (compact) for n = 2 .. kDirectMaxN
 constexpr int kDirectTable = 3 * (kDirectMaxN - 1) * kDirectMaxN * (2 * kDirectMaxN - 1) / 6;
@@ -513,31 +521,37 @@ __device__ void direct_level(T *sp, const T *sg, int n, T *scr) {
         W[q] = tab[(OP == 1 ? 2 : 1) * mm + q];
     }
     __syncthreads();
-    for (int q = tid; q < mm; q += nt) {  // A = S G
+    for (int q = tid; q < mm; q += nt) {  // A = S G (along y; x is carried)
         const int a = q / m, x = q - a * m;
         T v = T(0);
-        for (int y = 0; y < m; ++y) v = fma(S[a * m + y], sg[(y + 1) * LP + x + 1], v);
+        for (int y = 0; y < m; ++y) v = fma(S[y * m + a], sg[(y + 1) * LP + x + 1], v);
         A[q] = v;
     }
     __syncthreads();
-    for (int q = tid; q < mm; q += nt) {  // B = (A S) ./ lambda
+    const int half = m >> 1;
+    for (int q = tid; q < mm; q += nt) {  // B = (A S) ./ lambda, the x sum in mirror pairs
         const int a = q / m, b = q - a * m;
+        const T *Ar = A + a * m;
         T v = T(0);
-        for (int x = 0; x < m; ++x) v = fma(A[a * m + x], S[x * m + b], v);
+        for (int x = 0; x < half; ++x) {
+            const T p = (b & 1) ? Ar[x] - Ar[m - 1 - x] : Ar[x] + Ar[m - 1 - x];
+            v = fma(S[x * m + b], p, v);
+        }
+        if (m & 1) v = fma(S[half * m + b], Ar[half], v);
         B[q] = v * W[q];
     }
     __syncthreads();
-    for (int q = tid; q < mm; q += nt) {  // A = S B
+    for (int q = tid; q < mm; q += nt) {  // A = S B (along y)
         const int y = q / m, b = q - y * m;
         T v = T(0);
         for (int a = 0; a < m; ++a) v = fma(S[y * m + a], B[a * m + b], v);
         A[q] = v;
     }
     __syncthreads();
-    for (int q = tid; q < mm; q += nt) {  // psi = A S
+    for (int q = tid; q < mm; q += nt) {  // psi = A S (along x; x is the output index)
         const int y = q / m, x = q - y * m;
         T v = T(0);
-        for (int b = 0; b < m; ++b) v = fma(A[y * m + b], S[b * m + x], v);
+        for (int b = 0; b < m; ++b) v = fma(A[y * m + b], S[x * m + b], v);
         sp[(y + 1) * LP + x + 1] = v;
     }
     __syncthreads();
@@ -1346,8 +1360,19 @@ static cudaError_t init_direct_tables(int dev) {
         const int m = n - 1, mm = m * m;
         double *S = t64 + direct_off(n), *W5 = S + mm, *Wc = S + 2 * mm;
         const double sc = std::sqrt(2.0 / n);
-        for (int a = 0; a < m; ++a)
-            for (int y = 0; y < m; ++y) S[a * m + y] = sc * std::sin(pi * (a + 1) * (y + 1) / n);
+        // rows x < m / 2 from the sine, the others by S[m-1-x][b] = (-1)^b S[x][b];
+        // the middle row of an odd m exactly: sin(pi (b+1) / 2) is 0 or +-1
+        for (int x = 0; x < m; ++x)
+            for (int b = 0; b < m; ++b) {
+                double v;
+                if (2 * x + 1 < m)
+                    v = sc * std::sin(pi * (x + 1) * (b + 1) / n);
+                else if (2 * x + 1 == m)
+                    v = (b & 1) ? 0.0 : ((b >> 1) & 1 ? -sc : sc);
+                else
+                    v = (b & 1) ? -S[(m - 1 - x) * m + b] : S[(m - 1 - x) * m + b];
+                S[x * m + b] = v;
+            }
         for (int a = 0; a < m; ++a)
             for (int b = 0; b < m; ++b) {
                 const double ca = 2.0 * std::cos(pi * (a + 1) / n), cb = 2.0 * std::cos(pi * (b + 1) / n);
