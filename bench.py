@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--opt", action="append", default=[], metavar="KEY=VALUE",
+                    help="an lc_set_option key for the single-cavity contexts (profiling; repeatable)")
     return ap.parse_args()
 
 
@@ -256,8 +258,21 @@ KERNELS = {
 # traffic grows with the node count).  A kernel without a capture of its
 # current code reports null.
 #   k_smooth_colour<double,compact>: 12,728,576 B per launch at 1024^2 over
-#   1023^2 interior nodes = 12.163 B per node (12 B algorithmic).
-TRAFFIC_PER_NODE = {"k_smooth_colour<double,compact> (fine level, one colour phase)": 12728576 / 1023 ** 2}
+#   1023^2 interior nodes = 12.163 B per node (12 B algorithmic);
+#   k_rhs_stage (stage 2): 25,440,768 B = 24.31 B per node (32 B algorithmic;
+#   its output stays in L2 at this size);
+#   k_residual64_to32: 16,930,560 B = 16.18 B per node (20 B algorithmic);
+#   k_down<float> (110x22): 4,341,504 B = 4.15 B per node;
+#   k_up<float> (110x22): 18,192,384 B = 17.38 B per node.
+TRAFFIC_PER_NODE = {
+    "k_smooth_colour<double,compact> (fine level, one colour phase)": 12728576 / 1023 ** 2,
+    "k_rhs_stage (fused L(omega) + stage combination)": 25440768 / 1023 ** 2,
+    "k_rhs_stage (FP64 L(omega) + stage combination; option rhs64, the default)": 25440768 / 1023 ** 2,
+    "k_residual64_to32<compact> (FP64 residual, rounded to FP32)": 16930560 / 1023 ** 2,
+    "k_down<float,compact> (fine level: FP32 pre-smoothing + residual + restriction)": 4341504 / 1023 ** 2,
+    "k_up<float,compact> (fine level: FP32 post-smoothing + FP64 psi += e)": 18192384 / 1023 ** 2,
+}
+TRAFFIC_MEASURED_AT = 1024  # the per-node figures hold where the fields fit L2 as at 1024^2
 
 
 def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> dict:
@@ -289,7 +304,7 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
                                 f"{'FP64' if bound == 'alu64' else 'FP32'} FMA/clk x 2 flop x {mhz:.0f} MHz "
                                 f"(median SM clock under load)")}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    per_node = TRAFFIC_PER_NODE.get(name)
+    per_node = TRAFFIC_PER_NODE.get(name) if cav.N == TRAFFIC_MEASURED_AT else None
     roof["traffic"] = round(per_node * (cav.N - 1) ** 2) if per_node is not None else None
     roof["kernel"] = name
     roof["kernel_ms"] = ms
@@ -302,12 +317,21 @@ def roofline(lc, cav, precision: str, cycles_per_step: float, clocks: dict) -> d
     return roof
 
 
+def parse_opts(pairs) -> dict:
+    """--opt KEY=VALUE pairs as lc_set_option arguments."""
+    out = {}
+    for p in pairs:
+        k, _, v = p.partition("=")
+        out[k.strip()] = float(v)
+    return out
+
+
 def timed_run(lc, torch, dist, wl: Workload, precision: str, steps: int, warmup: int, eager: bool, world: int,
-              sample_clocks: int | None):
+              sample_clocks: int | None, extra: dict | None = None):
     """W warm-up steps, then K steps each bracketed by CUDA events on the
     context's stream, with an L2 flush between them."""
     opts = {"op": lc.LC_OP_COMPACT, "precision": lc.LC_PREC_MIXED if precision == "mixed" else lc.LC_PREC_FP64,
-            **SCHEDULE}
+            **SCHEDULE, **(extra or {})}
     if eager:
         opts["graph"] = 0
     cav = lc.Cavity(wl.N, wl.Re, wl.dt, wl.tol, **opts)
@@ -444,7 +468,8 @@ def run_ours(args, wl: Workload):
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    r = timed_run(lc, torch, dist, wl, args.precision, args.steps, args.warmup, args.eager, world, local)
+    extra = parse_opts(args.opt)
+    r = timed_run(lc, torch, dist, wl, args.precision, args.steps, args.warmup, args.eager, world, local, extra)
     cav = r["cav"]
     line = {
         "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -456,6 +481,8 @@ def run_ours(args, wl: Workload):
     line["config"]["vcycles_per_solve"] = float(r["cycles"].mean()) if len(r["cycles"]) else None
     if args.eager:
         line["config"]["launch"] = "eager (profiling)"
+    if extra:
+        line["config"]["options"] = extra
     line["gpu_launches"] = r["launches"]
     line["clocks"] = r["clocks"]
 
