@@ -449,7 +449,7 @@ static int mg_init(or_mg *mg, int N, int op) {
     mg->nuc = 16;
     mg->solver = OR_SOLVER_MG;
     mg->sor_sweeps = 16;
-    mg->beta = 1.0;
+    mg->beta = 1.1; /* relaxation of Eq. (15) in the smoother (the library's default) */
     for (int l = 0; l < nlev; ++l) {
         int n = N >> l;
         size_t m = (size_t)(n + 1) * (n + 1);

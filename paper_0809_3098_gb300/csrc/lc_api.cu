@@ -150,7 +150,7 @@ struct lc_ctx {
     int op = LC_OP_COMPACT, precision = LC_PREC_FP64;
     int nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, profile = 0, monitor = 0;
     int use_graph = 1;
-    double beta = 1.0, U = 1.0;
+    double beta = 1.1, U = 1.0;  // beta: the SOR relaxation of Eq. (15) in the smoother
     int solver = 0, sor_sweeps = 16;                    // 0 multigrid, 1 lexicographic SOR
     int coarse_direct = 1;  // the V-cycle ends at the first level below the fine one with <= 16 intervals, solved exactly
     int rhs64 = 1;  // mixed precision: L(omega) in FP64 (0: from the FP32 shadows)

@@ -74,7 +74,7 @@ struct lc_batch {
     std::vector<int> nv;  // levels the V-cycle visits (the last one solved exactly with coarse_direct)
     int coarse_direct = 1;
     std::vector<double> Re, dt;
-    double tol = 1e-10, beta = 1.0, U = 1.0;
+    double tol = 1e-10, beta = 1.1, U = 1.0;
     int op = LC_OP_COMPACT, nu1 = 2, nu2 = 1, nuc = 16, max_cycles = 100, advect = 1, coarse_max = 64;
     int use_graph = 1, rhs64 = 1;  // rhs64: L(omega) in FP64 (0: from the FP32 shadows)
     int pdl = 1;                   // programmatic dependent launch of the step's kernels

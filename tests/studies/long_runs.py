@@ -2,7 +2,8 @@
 arXiv:0809.3098, Sec. 3.2 monitors and the grid study of Sec. 4).
 
 Every case is one context of the CUDA library.  The cases advance in turns,
-`--every` steps at a time, until `--t-end` (or `--max-seconds`); after each
+`--every` steps at a time, until `--t-end`, `--max-seconds` or the paper's
+steady-state thresholds (a case that meets them stops); after each
 turn a case records the steady-state monitors of Eqs. (26)-(27) over its
 last step (the library's "monitor" option: max |d omega| / dt, RES_psi,
 RES_omega with 1/N read as 1/(N+1)) and psi at two probe nodes, so a
@@ -108,7 +109,7 @@ class Case:
 def run_cases(cases, t_end, every, max_seconds):
     t0 = time.perf_counter()
     while True:
-        live = [c for c in cases if c.steps * c.dt < t_end - 1e-12]
+        live = [c for c in cases if c.steps * c.dt < t_end - 1e-12 and c.steady_at is None]
         if not live or time.perf_counter() - t0 > max_seconds:
             break
         for c in live:
