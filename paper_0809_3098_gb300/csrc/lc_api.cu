@@ -697,7 +697,7 @@ int sync_status(lc_ctx *c) {
         if (status & kStatusTimeout) {
             // a barrier that gave up left arrivals behind: start the next one from zero
             unsigned zero2[2] = {0u, 0u};
-            LC_CUDA(cudaMemcpy(&c->ds()->bar_count, zero2, sizeof(unsigned), cudaMemcpyHostToDevice));
+            LC_CUDA(cudaMemcpy(&c->ds()->bar_count, zero2, sizeof(zero2), cudaMemcpyHostToDevice));
             return fail(LC_ERR_TIMEOUT, "a device-side grid barrier wait gave up");
         }
         if (status & kStatusNoConv) return fail(LC_ERR_NOCONV, "a Poisson solve reached max_cycles above tol");

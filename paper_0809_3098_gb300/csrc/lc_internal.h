@@ -56,7 +56,7 @@ struct DevState {
     double mon[3];    // max|d omega|/dt, RES_psi, RES_omega
     unsigned int arrive;  // blocks that have written their residual partial (fused finisher)
     unsigned int pad1;
-    unsigned int bar_count, bar_gen;  // grid barrier of the fused smoother
+    unsigned int bar_count, bar_gen;  // fused smoother's grid barrier: arrivals, and blocks that have left
     int log[kLogN];   // cycles per solve, ring buffer indexed by nsolves
 };
 

@@ -176,37 +176,52 @@ __global__ void __launch_bounds__(kBX *kBY)
 }
 
 // Grid-wide barrier between the colour phases of a cooperative launch (all
-// blocks co-resident).  Every wait is bounded: after kBarCycles SM clock
-// cycles (about 0.2 s) a block gives up, sets kStatusTimeout (reported as
-// LC_ERR_TIMEOUT; the host then resets the count) and goes on, so the kernel
-// always ends.  The last block to arrive resets the count before it releases
-// the others, so the next barrier starts from zero.  `expected` is the number
-// of arrivals that releases the barrier (gridDim.x; one more only in the
-// test that makes the wait run out).
+// blocks co-resident).  The arrival count only grows within a launch: barrier
+// k (k = 1, 2, ...) releases once it reaches k * expected, so an arrival is
+// one fence and one atomic add whose result nobody waits for, and a waiter
+// polls one word with acquire loads; nothing is reset between phases.  The
+// last block to leave the kernel (exit count, ds->bar_gen) sets both words
+// back to zero for the next launch.  Every wait is bounded: after kBarCycles
+// SM clock cycles (about 0.2 s) a block gives up, sets kStatusTimeout
+// (reported as LC_ERR_TIMEOUT) and goes on, so the kernel always ends.
+// `expected` is the number of arrivals per barrier (gridDim.x; one more only
+// in the test that makes the wait run out).
 constexpr long long kBarCycles = 400000000LL;
-__device__ __forceinline__ void grid_barrier(DevState *ds, unsigned expected) {
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void grid_barrier(DevState *ds, unsigned target) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &ds->bar_gen;
-        unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(&ds->bar_count, 1u) == expected - 1) {
-            ds->bar_count = 0;
-            __threadfence();
-            atomicAdd(&ds->bar_gen, 1u);
-        } else {
-            long long t0 = clock64();
-            while (*gen == g0) {
-                if (clock64() - t0 > kBarCycles) {
-                    atomicOr(&ds->status, kStatusTimeout);
-                    break;
-                }
-                __nanosleep(64);
+        __threadfence();  // the block's writes (ordered before by the block barrier) before the arrival
+        atomicAdd(&ds->bar_count, 1u);
+        long long t0 = clock64();
+        while ((int)(ld_acquire_gpu(&ds->bar_count) - target) < 0) {
+            if (clock64() - t0 > kBarCycles) {
+                atomicOr(&ds->status, kStatusTimeout);
+                break;
             }
         }
         __threadfence();
     }
     __syncthreads();
+}
+
+// Called once by every block as its last action: the last block out resets
+// the barrier words for the next launch.
+__device__ __forceinline__ void grid_barrier_exit(DevState *ds) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&ds->bar_gen, 1u) == gridDim.x - 1) {
+            ds->bar_count = 0;
+            ds->bar_gen = 0;
+            __threadfence();
+        }
+    }
 }
 
 // nsweeps colour sweeps of the smoother in one cooperative launch: the
@@ -225,14 +240,17 @@ __global__ void __launch_bounds__(256)
     const int hi = (int)((long long)items * (blockIdx.x + 1) / gridDim.x);
     const int wib = threadIdx.x >> 5, nwb = blockDim.x >> 5, lane = threadIdx.x & 31;
     const int ncol = OP == 1 ? 4 : 2;
+    const unsigned expected = gridDim.x + extra;
+    unsigned k = 0;  // barriers passed in this launch
     for (int s = 0; s < nsweeps; ++s)
         for (int col = 0; col < ncol; ++col) {
-            if (s > 0 || col > 0) grid_barrier(ds, gridDim.x + extra);
+            if (s > 0 || col > 0) grid_barrier(ds, ++k * expected);
             for (int w = lo + wib; w < hi; w += nwb) {
                 int b = w / nchunk, a = colour_a<OP>(w - b * nchunk, lane);
                 colour_item<T, OP, RELAX, true>(psi, g, N, P, col, beta, a, b);
             }
         }
+    grid_barrier_exit(ds);
 }
 
 // Residual of the fine level, full-weighted onto the coarse level; also zeroes
