@@ -61,6 +61,7 @@ class Case:
         self.hist = []
         self.seconds = 0.0
         self.steady_at = None
+        self.error = None  # set if the context reports an error (e.g. a non-finite state); the case stops
         self.thr = PAPER_THRESHOLDS[Re <= 20000]
         # probe nodes: the centre and a point in the bottom-right corner region
         self.probes = [(N // 2, N // 2), (int(round(0.9 * N)), int(round(0.1 * N)))]
@@ -82,6 +83,9 @@ class Case:
 
     def summary(self):
         h = self.hist
+        if not h:
+            return {"name": self.name, "N": self.N, "Re": self.Re, "dt": self.dt, "options": self.opts,
+                    "error": self.error, "monitors": []}
         k = max(1, len(h) // 10)
         last, prev = h[-k:], h[-2 * k:-k] if len(h) >= 2 * k else h[:k]
         mx_last = max(r["max_domega_dt"] for r in last)
@@ -95,7 +99,7 @@ class Case:
             trend = "not decaying"
         cyc = self.cav.cycle_log()
         return {"name": self.name, "N": self.N, "Re": self.Re, "dt": self.dt, "options": self.opts,
-                "steps": self.steps, "t_end": sig(self.steps * self.dt, 6), "seconds": round(self.seconds, 1),
+                "error": self.error, "steps": self.steps, "t_end": sig(self.steps * self.dt, 6), "seconds": round(self.seconds, 1),
                 "ms_per_step": sig(1e3 * self.seconds / max(self.steps, 1)),
                 "steady_at_step": self.steady_at, "thresholds": self.thr, "trend_last_tenth": trend,
                 "max_domega_dt_last_tenth": [min(r["max_domega_dt"] for r in last), mx_last],
@@ -109,13 +113,18 @@ class Case:
 def run_cases(cases, t_end, every, max_seconds):
     t0 = time.perf_counter()
     while True:
-        live = [c for c in cases if c.steps * c.dt < t_end - 1e-12 and c.steady_at is None]
+        live = [c for c in cases if c.steps * c.dt < t_end - 1e-12 and c.steady_at is None and c.error is None]
         if not live or time.perf_counter() - t0 > max_seconds:
             break
         for c in live:
             n = min(every, int(round((t_end - c.steps * c.dt) / c.dt)))
             if n > 0:
-                rec = c.advance(n)
+                try:
+                    rec = c.advance(n)
+                except Exception as e:  # a diverged case stops; the others go on
+                    c.error = f"{type(e).__name__} at t = {c.steps * c.dt:g}: {e}"
+                    print(json.dumps({"case": c.name, "error": c.error}), file=sys.stderr, flush=True)
+                    continue
                 if len(c.hist) % 20 == 0:
                     print(json.dumps({"case": c.name, **rec}), file=sys.stderr, flush=True)
 
