@@ -260,7 +260,8 @@ KERNELS = {
 # traffic grows with the node count).  A kernel without a capture of its
 # current code reports null.
 #   k_smooth_colour<double,compact>: 12,728,576 B per launch at 1024^2 over
-#   1023^2 interior nodes = 12.163 B per node (12 B algorithmic);
+#   1023^2 interior nodes = 12.163 B per node (12 B algorithmic); its
+#   relaxed form (beta != 1, the default): 12,571,648 B = 12.01 B per node;
 #   k_rhs_stage (stage 2): 25,440,768 B = 24.31 B per node (32 B algorithmic;
 #   its output stays in L2 at this size);
 #   k_residual64_to32: 16,930,560 B = 16.18 B per node (20 B algorithmic);
@@ -268,6 +269,7 @@ KERNELS = {
 #   k_up<float> (110x22): 18,192,384 B = 17.38 B per node.
 TRAFFIC_PER_NODE = {
     "k_smooth_colour<double,compact> (fine level, one colour phase)": 12728576 / 1023 ** 2,
+    "k_smooth_colour<double,compact,relaxed> (fine level, one colour phase, beta != 1)": 12571648 / 1023 ** 2,
     "k_rhs_stage (fused L(omega) + stage combination)": 25440768 / 1023 ** 2,
     "k_rhs_stage (FP64 L(omega) + stage combination; option rhs64, the default)": 25440768 / 1023 ** 2,
     "k_residual64_to32<compact> (FP64 residual, rounded to FP32)": 16930560 / 1023 ** 2,
