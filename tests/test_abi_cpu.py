@@ -131,3 +131,24 @@ def test_noalloc_monitor_rejects_bad_arguments_on_the_host(L):
     assert lc.lc_monitor_noalloc(8, p, p, p, p, 9, 1.0, 0) == lc.LC_ERR_ARG  # NULL output
     assert lc.lc_monitor_noalloc(8, p, p, p, p, 9, 0.0, p) == lc.LC_ERR_ARG  # dt <= 0
     assert lc.lc_monitor_noalloc(0, p, p, p, p, 9, 1.0, p) == lc.LC_ERR_ARG  # N < 1
+
+
+def _levels(N):
+    n, lv = N, 1
+    while n % 2 == 0 and n >= 4:
+        n //= 2
+        lv += 1
+    return lv
+
+
+@pytest.mark.parametrize("N", [8, 10, 12, 14, 16, 24, 32, 40, 56, 96, 128, 160, 224, 320, 384, 768, 1024, 2048, 8192])
+def test_exact_coarse_level_choice(L, N):
+    """The V-cycle ends at the first level below the fine one with at most 16
+    intervals (the exact solve), or, with coarse_direct = 0, at the 2-, 3-, 5-
+    or 7-interval grid: the same rule the oracle's mg_set_direct applies."""
+    h = lc.lc_create(N, 1000.0, 0.0, 1e-10)
+    first = next(l for l in range(1, _levels(N)) if N >> l <= 16)
+    assert lc.lc_get_params(h)[5] == first + 1
+    assert lc.lc_set_option(h, "coarse_direct", 0) == lc.LC_OK
+    assert lc.lc_get_params(h)[5] == _levels(N)
+    lc.lc_destroy(h)
