@@ -449,7 +449,7 @@ constexpr int kMaxBatch = 256;
 // device).  Mixed precision: the fine level holds psi64/g64 (FP64) and the
 // FP32 correction hierarchy eA/eB/g32 (g32[0] is the FP32 residual).
 struct BatchCav {
-    int N, nlev, lc;  // intervals, multigrid levels, first level of the one-block coarse cycle
+    int N, nlev, lc;  // intervals, levels the V-cycle visits, first level of the one-block coarse cycle
     int P[kMaxLevels];
     double Re, dt;
     double *psi64, *g64;
